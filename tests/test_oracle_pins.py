@@ -1,0 +1,370 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: admittances against hand-worked
+values and an ideal-transformer circuit model, flows against complex power
+S = V conj(I), derivatives against finite differences, TRON against the KKT
+conditions and brute force, the closed forms against generic dense solves and
+1-D search, the whole ADMM against an independent SciPy solve of eq. acopf.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from acopf_ref import branch_power, cost, mismatch, solve_acopf
+from paper_2110_06879_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TWO_PI = 2.0 * np.pi
+
+
+def test_admittance_golden(oracle_mod):
+    """Section II-A admittance definitions, worked by hand (golden fixture)."""
+    rows = np.loadtxt(os.path.join(HERE, "golden", "admittance_cases.txt"))
+    for row in rows:
+        r, x, b, tap, shift = row[:5]
+        got = oracle_mod.admittance(r, x, b, tap, shift)
+        np.testing.assert_allclose(got, row[5:], atol=1e-12, rtol=0)
+
+
+def test_flows_match_circuit_model(oracle_mod):
+    """eq. (pij)-(qji) with the pi-model entries equal S = V conj(I) of the
+    branch circuit (ideal transformer, series impedance, split charging)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        r, x, b = rng.uniform(0, 0.05), rng.uniform(0.01, 0.5), rng.uniform(0, 0.3)
+        tap, shift = rng.uniform(0.8, 1.2), rng.uniform(-0.5, 0.5)
+        Y = oracle_mod.admittance(r, x, b, tap, shift)
+        vi, vj = rng.uniform(0.9, 1.1, 2)
+        ti, tj = rng.uniform(-1, 1, 2)
+        fl = oracle_mod.branch_flows(Y, [vi, vj, ti, tj, 0, 0])
+
+        class G:  # one-branch grid for the circuit model
+            f_bus = np.array([0]); t_bus = np.array([1])
+        G.r, G.x, G.b = np.array([r]), np.array([x]), np.array([b])
+        G.tap, G.shift = np.array([tap]), np.array([shift])
+        V = np.array([vi * np.exp(1j * ti), vj * np.exp(1j * tj)])
+        sf, st = branch_power(V, G)
+        np.testing.assert_allclose(fl, [sf[0].real, sf[0].imag, st[0].real, st[0].imag],
+                                   rtol=1e-12, atol=1e-12)
+
+
+def _random_prob(oracle_mod, rng, lt=None, rt=None, rate=None):
+    r, x, b = rng.uniform(0.002, 0.03), 0.0, rng.uniform(0, 0.05)
+    x = r * rng.uniform(3, 10)
+    Y = oracle_mod.admittance(r, x, b, 1.0, 0.0)
+    vi, vj, th = rng.uniform(0.95, 1.05), rng.uniform(0.95, 1.05), rng.uniform(-0.2, 0.2)
+    fl = oracle_mod.branch_flows(Y, [vi, vj, th, 0, 0, 0])
+    rate = rate if rate is not None else 1.3 * max(np.hypot(fl[0], fl[1]), np.hypot(fl[2], fl[3]))
+    slo = -(0.99 * rate) ** 2
+    xbar = np.concatenate([fl + rng.normal(0, 0.05, 4),
+                           [vi ** 2 + rng.normal(0, 0.01), th + rng.normal(0, 0.02),
+                            vj ** 2 + rng.normal(0, 0.01), rng.normal(0, 0.02)]])
+    z = rng.normal(0, 1e-3, 8)
+    y = rng.normal(0, 5.0, 8)
+    rho = np.array([1e3] * 4 + [1e4] * 4)
+    lt = rng.uniform(0, 5, 2) if lt is None else lt
+    rt = 1e3 if rt is None else rt
+    bp = oracle_mod.branch_prob(Y, [0.94, 0.94, -TWO_PI, -TWO_PI, slo, slo],
+                                [1.06, 1.06, TWO_PI, TWO_PI, 0, 0], xbar, z, y, rho, lt, rt)
+    x0 = np.array([1.0, 1.0, 0.0, 0.0, max(slo, -fl[0] ** 2 - fl[1] ** 2),
+                   max(slo, -fl[2] ** 2 - fl[3] ** 2)])
+    return bp, x0, Y
+
+
+def _F_circuit(bp, x):
+    """eq. branch with the flows taken from the circuit model (complex power)."""
+    Y = np.array(bp.Y[:])
+    # recover a one-branch circuit from the unit-tap entries: y = -(g_ij + j b_ij)
+    ys = -(Y[2] + 1j * Y[3])
+    ysh2 = (Y[0] + 1j * Y[1]) - ys
+
+    class G:
+        f_bus = np.array([0]); t_bus = np.array([1])
+        tap = np.array([1.0]); shift = np.array([0.0])
+    zser = 1.0 / ys
+    G.r, G.x, G.b = np.array([zser.real]), np.array([zser.imag]), np.array([2 * ysh2.imag])
+    V = np.array([x[0] * np.exp(1j * x[2]), x[1] * np.exp(1j * x[3])])
+    sf, st = branch_power(V, G)
+    u = np.array([sf[0].real, sf[0].imag, st[0].real, st[0].imag,
+                  x[0] ** 2, x[2], x[1] ** 2, x[3]])
+    rr = u - np.array(bp.xbar[:]) + np.array(bp.z[:])
+    F = np.sum(np.array(bp.y[:]) * rr + 0.5 * np.array(bp.rho[:]) * rr ** 2)
+    for e in range(2):
+        h = u[2 * e] ** 2 + u[2 * e + 1] ** 2 + x[4 + e]
+        F += bp.lt[e] * h + 0.5 * bp.rt * h * h
+    return F
+
+
+def test_branch_function_matches_definition(oracle_mod):
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        bp, x0, _ = _random_prob(oracle_mod, rng)
+        x = x0 + np.array([0.01, -0.02, 0.05, -0.03, 0.0, 0.0])
+        f, _, _ = oracle_mod.branch_fgh(bp, x)
+        assert f == pytest.approx(_F_circuit(bp, x), rel=1e-11, abs=1e-9)
+
+
+def test_branch_gradient_hessian_finite_differences(oracle_mod):
+    rng = np.random.default_rng(7)
+    for _ in range(30):
+        bp, x0, _ = _random_prob(oracle_mod, rng)
+        x = x0 + rng.normal(0, 0.02, 6) * np.array([1, 1, 1, 1, 0, 0])
+        x[4:] = x0[4:] * 0.5
+        f, g, H = oracle_mod.branch_fgh(bp, x)
+        # fourth-order central differences
+        gfd = np.zeros(6)
+        Hfd = np.zeros((6, 6))
+        for k in range(6):
+            h = 1e-4 * max(1.0, abs(x[k]))
+            e = np.zeros(6); e[k] = h
+            fp1, gp1, _ = oracle_mod.branch_fgh(bp, x + e)
+            fm1, gm1, _ = oracle_mod.branch_fgh(bp, x - e)
+            fp2, gp2, _ = oracle_mod.branch_fgh(bp, x + 2 * e)
+            fm2, gm2, _ = oracle_mod.branch_fgh(bp, x - 2 * e)
+            gfd[k] = (-fp2 + 8 * fp1 - 8 * fm1 + fm2) / (12 * h)
+            Hfd[:, k] = (-gp2 + 8 * gp1 - 8 * gm1 + gm2) / (12 * h)
+        scale_g = max(1.0, np.abs(g).max())
+        scale_H = max(1.0, np.abs(H).max())
+        assert np.abs(gfd - g).max() <= 1e-7 * scale_g
+        assert np.abs(Hfd - H).max() <= 1e-7 * scale_H
+        assert np.abs(H - H.T).max() <= 1e-12 * scale_H
+
+
+def _proj_grad(x, g, lo, hi):
+    return np.clip(x - g, lo, hi) - x
+
+
+def test_tron_kkt(oracle_mod):
+    """Lin-More TRON returns a point whose projected gradient vanishes."""
+    rng = np.random.default_rng(11)
+    for it in range(200):
+        tight = it % 3 == 0
+        bp, x0, _ = _random_prob(oracle_mod, rng, rate=0.3 if tight else None)
+        _, g0, _ = oracle_mod.branch_fgh(bp, x0)
+        x, status, st = oracle_mod.tron(bp, x0)
+        assert status == 0, st
+        _, g, _ = oracle_mod.branch_fgh(bp, x)
+        lo, hi = np.array(bp.lo[:]), np.array(bp.hi[:])
+        assert np.all(x >= lo) and np.all(x <= hi)
+        # KKT of the bound-constrained problem, relative to the starting gradient
+        pg = np.abs(_proj_grad(x, g, lo, hi)).max()
+        assert pg <= 1e-10 * max(1.0, np.abs(g0).max()), (it, pg, st)
+
+
+def test_tron_brute_force_small(oracle_mod):
+    """TRON's local solution is the best point of a 4-D grid search (slacks
+    eliminated in closed form) refined by a local solve, or at least as good."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(13)
+    for it in range(12):
+        bp, x0, _ = _random_prob(oracle_mod, rng, rate=0.3 if it % 2 else None)
+        x, status, _ = oracle_mod.tron(bp, x0)
+        f_tron = oracle_mod.branch_fgh(bp, x)[0]
+        lo, hi = np.array(bp.lo[:]), np.array(bp.hi[:])
+
+        def F_elim(v4):
+            xx = np.concatenate([v4, [0.0, 0.0]])
+            fl = oracle_mod.branch_flows(np.array(bp.Y[:]), xx)
+            for e in range(2):
+                pq = fl[2 * e] ** 2 + fl[2 * e + 1] ** 2
+                xx[4 + e] = np.clip(-pq - bp.lt[e] / bp.rt, lo[4 + e], 0.0)
+            return _F_circuit(bp, xx), xx
+
+        # coarse grid around the targets (the penalties keep the solution there)
+        tgt = np.array([np.sqrt(max(bp.xbar[4], 0.5)), np.sqrt(max(bp.xbar[6], 0.5)),
+                        bp.xbar[5], bp.xbar[7]])
+        axes = [np.linspace(lo[0], hi[0], 13), np.linspace(lo[1], hi[1], 13),
+                tgt[2] + np.linspace(-0.3, 0.3, 13), tgt[3] + np.linspace(-0.3, 0.3, 13)]
+        best = []
+        for a in axes[0]:
+            for b_ in axes[1]:
+                for c in axes[2]:
+                    for d in axes[3]:
+                        best.append((F_elim(np.array([a, b_, c, d]))[0], (a, b_, c, d)))
+        best.sort(key=lambda t: t[0])
+        f_best = np.inf
+        for _, start in best[:5]:
+            res = minimize(lambda v: F_elim(v)[0], np.array(start), method="L-BFGS-B",
+                           bounds=list(zip(lo[:4], hi[:4])),
+                           options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 2000})
+            f_best = min(f_best, res.fun)
+        assert f_tron <= f_best + 1e-7 * max(1.0, abs(f_best)), (it, f_tron, f_best)
+
+
+def test_gen_closed_form_brute_force(oracle_mod):
+    """eq. qp-bound for a generator: clip(Q^-1 c) is the 1-D minimiser."""
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        c2, c1 = rng.uniform(0, 1e3), rng.uniform(0, 5e3)
+        rho = 10 ** rng.uniform(0, 4)
+        xbar, z, y = rng.normal(0, 2), rng.normal(0, 0.1), rng.normal(0, 3e3)
+        lo, hi = sorted(rng.uniform(-1, 4, 2))
+        got = oracle_mod.gen_solve(c2, c1, rho, xbar, z, y, lo, hi)
+        phi = lambda p: c2 * p * p + c1 * p + y * (p - xbar + z) + 0.5 * rho * (p - xbar + z) ** 2
+        grid = np.linspace(lo, hi, 200001)
+        k = np.argmin(phi(grid))
+        assert lo <= got <= hi
+        assert phi(got) <= phi(grid[k]) + 1e-9 * max(1, abs(phi(grid[k])))
+        assert abs(got - grid[k]) <= 2 * (hi - lo) / 200000 + 1e-12
+
+
+def _own_incidence(grid):
+    rows = [[] for _ in range(grid.nbus)]
+    for l in range(grid.nbranch):
+        rows[grid.f_bus[l]].append(("f", l))
+        rows[grid.t_bus[l]].append(("t", l))
+    for g in range(grid.ngen):
+        rows[grid.gen_bus[g]].append(("g", g))
+    return rows
+
+
+def test_csr_matches_independent_build(oracle_mod):
+    """Incidence rows: branch ends by branch id (from before to), then gens."""
+    grid = synth.sized_grid(500, seed=4)
+    o = oracle_mod.Oracle(grid)
+    row, col = o.csr()
+    nl = grid.nbranch
+    ent = np.concatenate([np.arange(2 * nl), 2 * nl + np.arange(grid.ngen)])
+    bus = np.concatenate([np.stack([grid.f_bus, grid.t_bus], 1).ravel(), grid.gen_bus])
+    order = np.lexsort((ent, bus))
+    exp_col = ent[order].astype(np.int32)
+    exp_row = np.concatenate([[0], np.cumsum(np.bincount(bus, minlength=grid.nbus))]).astype(np.int32)
+    assert np.array_equal(row, exp_row) and np.array_equal(col, exp_col)
+
+
+def test_bus_update_dense_kkt(oracle_mod):
+    """eq. qp-bus: the bus copies solve the dense KKT system of each bus QP."""
+    grid = synth.tiny_grid(1)
+    o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4)
+    o.solve(tol=0.0, max_iter=7)
+    u, z, y, rho = (o.get(k) for k in (oracle_mod.U, oracle_mod.Z, oracle_mod.Y, oracle_mod.RHO))
+    # z, y after the last iteration: recover the values the bus update used
+    # by re-running 6 iterations and taking z, y of that state
+    o6 = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4)
+    o6.solve(tol=0.0, max_iter=6)
+    z6, y6 = o6.get(oracle_mod.Z), o6.get(oracle_mod.Y)
+    xbar = o.get(oracle_mod.XBAR)
+    ng, nl = grid.ngen, grid.nbranch
+    cb = lambda l, k: 2 * ng + 8 * l + k
+    for i, ents in enumerate(_own_incidence(grid)):
+        # variables: w, then per entry (p copy, q copy); theta handled apart
+        var_c, a_p, a_q = [], [], []
+        wc, tc = [], []
+        for kind, idx in ents:
+            if kind == "g":
+                var_c += [2 * idx, 2 * idx + 1]; a_p += [1.0, 0.0]; a_q += [0.0, 1.0]
+            else:
+                off = 0 if kind == "f" else 2
+                var_c += [cb(idx, off), cb(idx, off + 1)]; a_p += [-1.0, 0.0]; a_q += [0.0, -1.0]
+                wc.append(cb(idx, 4 if kind == "f" else 6)); tc.append(cb(idx, 5 if kind == "f" else 7))
+        t = lambda c: u[c] + z6[c] + y6[c] / rho[c]
+        qw = sum(rho[c] for c in wc)
+        n = 1 + len(var_c)
+        Q = np.diag([qw] + [rho[c] for c in var_c])
+        cvec = np.array([sum(rho[c] * t(c) for c in wc)] + [rho[c] * t(c) for c in var_c])
+        A = np.array([[-grid.gs[i]] + a_p, [grid.bs[i]] + a_q])
+        bvec = np.array([grid.pd[i], grid.qd[i]])
+        K = np.block([[Q, A.T], [A, np.zeros((2, 2))]])
+        sol = np.linalg.solve(K, np.concatenate([cvec, bvec]))
+        xs = sol[:n]
+        got = np.array([xbar[wc[0]]] + [xbar[c] for c in var_c])
+        np.testing.assert_allclose(got, xs, rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(A @ got, bvec, atol=1e-10)
+        th_exp = 0.0 if i == grid.ref_bus else sum(rho[c] * t(c) for c in tc) / sum(rho[c] for c in tc)
+        for c in tc:
+            assert xbar[c] == pytest.approx(th_exp, abs=1e-12)
+        for c in wc:
+            assert xbar[c] == xbar[wc[0]]
+
+
+def test_z_and_y_updates(oracle_mod):
+    """Line 5-6 of Algorithm 1: z is the stationary point of
+    lam z + beta/2 z^2 + y (r0 + z) + rho/2 (r0 + z)^2; y += rho (r0 + z)."""
+    grid = synth.tiny_grid(2)
+    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5)
+    a = oracle_mod.Oracle(grid, **kw); a.solve(tol=0.0, max_iter=3)
+    b = oracle_mod.Oracle(grid, **kw); b.solve(tol=0.0, max_iter=4)
+    assert b.residuals()["outer_iters"] == 0
+    y0, lam0 = a.get(oracle_mod.Y), a.get(oracle_mod.LAMBDA)
+    u, xb, z, y, rho = (b.get(k) for k in (oracle_mod.U, oracle_mod.XBAR, oracle_mod.Z,
+                                            oracle_mod.Y, oracle_mod.RHO))
+    beta = b.residuals()["beta"]
+    assert beta == 1e5
+    r0 = u - xb
+    # stationarity checked by bracketing the 1-D minimiser numerically
+    for c in range(len(z)):
+        phi = lambda v: lam0[c] * v + 0.5 * beta * v * v + y0[c] * (r0[c] + v) + 0.5 * rho[c] * (r0[c] + v) ** 2
+        d = 1e-6 * max(1e-6, abs(z[c]))
+        assert phi(z[c]) <= phi(z[c] + d) + 1e-9 and phi(z[c]) <= phi(z[c] - d) + 1e-9
+    np.testing.assert_allclose(y - y0, rho * (r0 + z), rtol=1e-9, atol=1e-9)
+
+
+def test_outer_update_rule(oracle_mod):
+    """Algorithm 1 line 8 with max_inner = 1: one outer update per iteration.
+    lam <- Proj(lam + beta z); beta grows by beta_factor only when ||z|| did
+    not drop below z_decay of its value at the previous outer update."""
+    grid = synth.tiny_grid(2)
+    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5, max_inner=1, lambda_max=50.0)
+    runs = []
+    for k in (1, 2, 3):
+        o = oracle_mod.Oracle(grid, **kw)
+        o.solve(tol=0.0, max_iter=k)
+        runs.append(o)
+    z1, z2, z3 = (r.get(oracle_mod.Z) for r in runs)
+    l1, l2, l3 = (r.get(oracle_mod.LAMBDA) for r in runs)
+    b = [r.residuals()["beta"] for r in runs]
+    np.testing.assert_allclose(l1, np.clip(1e5 * z1, -50, 50), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(l2, np.clip(l1 + b[0] * z2, -50, 50), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(l3, np.clip(l2 + b[1] * z3, -50, 50), rtol=1e-12, atol=1e-12)
+    n1, n2, n3 = (np.linalg.norm(v) for v in (z1, z2, z3))
+    assert b[0] == 1e5
+    assert b[1] == (6e5 if n2 > 0.8 * n1 else 1e5)
+    assert b[2] == (b[1] * 6 if n3 > 0.8 * n2 else b[1])
+
+
+def test_cold_start_state(oracle_mod):
+    """Section IV-B: mid-bound generation and magnitudes, zero angles, flows
+    from those voltages, consensus at the start, zero multipliers."""
+    grid = synth.tiny_grid(0)
+    o = oracle_mod.Oracle(grid)
+    u, xb = o.get(oracle_mod.U), o.get(oracle_mod.XBAR)
+    assert np.array_equal(u, xb)
+    ng = grid.ngen
+    np.testing.assert_allclose(u[0:2 * ng:2], 0.5 * (grid.pmin + grid.pmax))
+    V = 0.5 * (grid.vmin + grid.vmax) + 0j
+    sf, st = branch_power(V, grid)
+    ub = u[2 * ng:].reshape(-1, 8)
+    np.testing.assert_allclose(ub[:, 0], sf.real, atol=1e-12)
+    np.testing.assert_allclose(ub[:, 3], st.imag, atol=1e-12)
+    assert np.all(ub[:, 5] == 0) and np.all(ub[:, 7] == 0)
+    for k in (oracle_mod.Z, oracle_mod.Y, oracle_mod.LAMBDA):
+        assert not np.any(o.get(k))
+
+
+def test_one_level_keeps_z_zero(oracle_mod):
+    grid = synth.tiny_grid(0)
+    o = oracle_mod.Oracle(grid, two_level=0, rho_pq=1e3, rho_va=1e4)
+    o.solve(tol=0.0, max_iter=20)
+    assert not np.any(o.get(oracle_mod.Z))
+
+
+@pytest.mark.slow
+def test_tiny_admm_solves_acopf(oracle_mod):
+    """Whole method on the 30-bus grid: the converged point satisfies the AC
+    power balance to 1e-4 pu and its cost matches an independent NLP solve of
+    eq. acopf to 1e-4 relative; it is no worse than the built-in point."""
+    grid = synth.tiny_grid(0)
+    o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4, beta0=1e5)
+    status = o.solve(tol=1e-4, max_iter=20000)
+    res = o.residuals()
+    assert status == 0, res
+    assert res["z_norm"] <= 1e-4
+    sol = o.finalize()
+    mis = mismatch(sol["vm"], sol["va"], sol["pg"], sol["qg"], grid)
+    assert np.abs(mis).max() <= 1e-4
+    assert sol["max_viol"] <= 1e-4
+    ref = solve_acopf(grid)
+    assert ref["success"]
+    assert abs(sol["objective"] - ref["objective"]) <= 1e-4 * ref["objective"]
+    assert sol["objective"] <= cost(grid.pg0, grid) * (1 + 1e-4)
