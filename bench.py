@@ -1,0 +1,307 @@
+"""Benchmark: ADMM iterations/s of the component-decomposed ACOPF solver on a
+synthetic 70,000-bus grid (88,207 branches, 10,390 generators, Table 1 shape).
+
+A step is one inner ADMM iteration of Algorithm 1 over the whole grid:
+branch_tron (every branch subproblem) then bus_dual (generator, bus, z and y
+updates, residual reduction, loop control).  The grid state (~80 MB) fits in
+L2, so L2 is flushed (256 MiB write) between timed steps.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iterations/s, 70k-bus synthetic grid"
+C_RESIDUALS_BYTES = 72   # sizeof(admm_residuals): 4 int32 + 7 double
+UNIT = "iter/s"
+
+# Algorithmic FP64 operations of the branch subproblem solver, counted from
+# the method's formulas (an FMA counts 2, sin and cos 1 each, comparisons and
+# min/max 0).  Multiplied by the per-solve counters the kernel reports.
+FLOPS = dict(
+    fgh=268,        # flows + first/second derivatives + AL assembly of g and H
+    f=66,           # flows + function value
+    cauchy=103,     # projected step (12) + ||s|| (12) + q(s) (84) per trial, less shared
+    tron_iter=330,  # subspace: gc (72), scaled Cholesky (~110), PCG set-up, ratio test
+    cg=150,         # one PCG iteration: Hp (72), dots, TR test, preconditioner solve (~50)
+    ps=110,         # one projected-search trial: step (12) + q(s) (84) + descent test
+    al=34,          # one AL pass: flows at the solution + multiplier update
+)
+
+
+def algorithmic_flops(stats: dict) -> float:
+    return (FLOPS["fgh"] * stats["fgh_evals"] + FLOPS["f"] * stats["f_evals"]
+            + FLOPS["cauchy"] * stats["cauchy_trials"] + FLOPS["tron_iter"] * stats["tron_iters"]
+            + FLOPS["cg"] * stats["cg_iters"] + FLOPS["ps"] * stats["ps_trials"]
+            + FLOPS["al"] * stats["al_passes"])
+
+
+def fp64_peak_gflops():
+    """FP64 peak of a GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA
+    per clock per SM (measured FMA issue rate) x 2 flops x
+    2.07 GHz."""
+    return 152 * 2 * 2 * 2.070
+
+
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+                for n, v in zip(names, r[3:7]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(nbus, seed):
+    from paper_2110_06879_gb300 import synth
+    grid = synth.sized_grid(nbus, seed=seed)
+    rp, rv, so = synth.penalties_for(nbus)
+    return grid, dict(rho_pq=rp, rho_va=rv, obj_scale=so)
+
+
+def cpu_baseline(grid, opts, seconds=15.0):
+    """The oracle as it stands on the host cores: iterations after a one-
+    iteration cold start, until about `seconds` of CPU time are spent."""
+    import oracle
+    o = oracle.Oracle(grid, **opts)
+    o.solve(tol=0.0, max_iter=1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.solve(tol=0.0, max_iter=1, warm_start=True)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} warm iterations (iterations 2..{n + 1} of a cold solve) of the "
+                      f"{grid.nbus}-bus grid, single-threaded C oracle"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    grid, opts = make_workload(args.nbus, args.seed)
+    import oracle
+    o = oracle.Oracle(grid, **opts)
+    o.solve(tol=0.0, max_iter=1)
+    for _ in range(args.warmup):
+        o.solve(tol=0.0, max_iter=1, warm_start=True)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.solve(tol=0.0, max_iter=1, warm_start=True)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": workload_config(grid, opts, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} warm ADMM iterations of the {grid.nbus}-bus "
+                                       "grid after a cold start and warm-up, single-threaded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(grid, opts, args):
+    return {"workload": f"synthetic {grid.nbus}-bus grid ({grid.nbranch} branches, {grid.ngen} "
+                        f"generators), one inner ADMM iteration per step after a cold start",
+            "nbus": grid.nbus, "nbranch": grid.nbranch, "ngen": grid.ngen, "seed": args.seed,
+            "rho_pq": opts["rho_pq"], "rho_va": opts["rho_va"], "obj_scale": opts["obj_scale"],
+            "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2110_06879_gb300 import admm
+
+    grid, opts = make_workload(args.nbus, args.seed + rank)
+    stream = torch.cuda.current_stream()
+    s = admm.Solver(grid, stream=stream, **opts)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up: cold start + W iterations
+    s.solve(tol=0.0, max_iter=max(args.warmup, 3))
+    torch.cuda.synchronize()
+    st0 = s.stats()
+    stats_acc = {k: 0 for k in st0}
+    branch_ms, iter_ms, bus_ms = [], [], []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            p = s.profile_iterations(1)
+            st = s.stats()
+            for k in stats_acc:
+                stats_acc[k] += st[k]
+            branch_ms.append(p["branch_ms"])
+            bus_ms.append(p["bus_ms"])
+            iter_ms.append(p["iter_ms"])
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    t_total = sum(iter_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = ws * args.steps / t_total
+
+    # dominant kernel roofline (FP64 ALU bound)
+    b_mean = sum(branch_ms) / len(branch_ms)
+    flops_per_launch = algorithmic_flops(stats_acc) / args.steps
+    achieved = flops_per_launch / (b_mean * 1e-3) / 1e9
+    peak = fp64_peak_gflops()
+
+    # end to end through the public API with host buffers
+    pd = torch.tensor(grid.pd, dtype=torch.float64).pin_memory().numpy()
+    qd = torch.tensor(grid.qd, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_loads(pd, qd)
+        s.solve_async(tol=0.0, max_iter=1, warm_start=True)
+        s.residuals()               # device -> host read of the step's result
+    e2e_dt = time.perf_counter() - t0
+    e2e = {"value": args.steps / e2e_dt * ws, "unit": UNIT,
+           "h2d_bytes_per_step": int(pd.nbytes + qd.nbytes),
+           "d2h_bytes_per_step": C_RESIDUALS_BYTES}
+
+    # time to residual 1e-3 from a cold start (whole solve, one graph launch)
+    tt = None
+    if args.time_to_tol:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st_code = s.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        r = s.residuals()
+        sol = s.solution()
+        tt = {"tol": 1e-3, "seconds": ev0.elapsed_time(ev1) / 1e3, "iters": r["iters"],
+              "status": admm.lib().admm_status_string(r["status"]).decode(),
+              "primal": r["primal"], "dual": r["dual"], "z_norm": r["z_norm"],
+              "objective": sol["objective"], "max_viol": sol["max_viol"]}
+        del st_code
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": sum(iter_ms) / len(iter_ms),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(grid, opts, args),
+                "roofline": {"kernel": "branch_tron", "bound": "alu", "achieved": achieved,
+                             "peak": peak, "unit": "GFLOP/s (FP64)", "frac": achieved / peak,
+                             "traffic": None, "ms_per_launch": b_mean,
+                             "flops_per_launch": flops_per_launch},
+                "bus_dual_ms": sum(bus_ms) / len(bus_ms),
+                "branch_solves_per_s": value * grid.nbranch,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * args.steps * ws,
+                "tron_stats_per_step": {k: v / args.steps for k, v in stats_acc.items()}}
+        if tt is not None:
+            line["time_to_tol"] = tt
+        if args.cpu_baseline and ws >= 1:
+            line["cpu_baseline"] = cpu_baseline(grid, opts, args.cpu_seconds)
+        print(json.dumps(line))
+    s.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nbus", type=int, default=70000)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false")
+    ap.add_argument("--tol-max-iter", type=int, default=5000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * admm.h -- C ABI of libadmm.so, a GB300 (sm_103a) FP64 implementation of the
+ * component-decomposed two-level ADMM for AC optimal power flow of Kim & Kim,
+ * "Accelerated Computation and Tracking of AC Optimal Power Flow Solutions
+ * Using GPUs" (arXiv 2110.06879).
+ *
+ * One handle holds one grid resident on the current CUDA device.  Every
+ * iteration of Algorithm 1 runs on the device:
+ *   branch_tron  -- eq. branch per branch (TRON inside an augmented Lagrangian on
+ *                   the line limits, Section II-C / III-B), one thread per branch;
+ *   bus_dual     -- eq. qp-bound for generators, eq. qp-bus per bus over a CSR
+ *                   incidence map (no atomics), the z update (eq. qp-bound with
+ *                   infinite bounds), the y update (Section III-B) and the
+ *                   primal/dual residual reduction with a device convergence flag;
+ * captured once as a CUDA graph whose conditional WHILE node repeats the
+ * iteration until the device flag says stop, so a solve costs one graph launch
+ * and one stream synchronisation (Section III: no host-device traffic during
+ * the iteration).
+ *
+ * Conventions
+ *   - Every pointer argument is a HOST pointer unless its name starts with d_.
+ *   - The caller owns every buffer it passes; the library copies inputs during
+ *     the call and writes outputs before it returns.  The handle owns all device
+ *     memory it allocates, until admm_destroy.
+ *   - Indices are 0-based int32.  Powers, voltages and impedances are per unit on
+ *     base_mva; angles (and the branch shift) in radians; costs in $/MW^2h,
+ *     $/MWh and $/h (MATPOWER units: c2' = c2 base^2, c1' = c1 base on per-unit
+ *     power).
+ *   - Functions return ADMM_OK (0) or a status below; no exception crosses the
+ *     ABI.  A handle is not thread-safe; calls on one handle must be serialised.
+ *   - Canonical coupling order (length m = 2 ngen + 8 nbranch), used by every
+ *     per-coupling output: [2g] p_g, [2g+1] q_g for generator g, then for branch
+ *     l at 2 ngen + 8 l + k, k = 0..7: p_ij, q_ij, p_ji, q_ji, w_i(ij),
+ *     theta_i(ij), w_j(ij), theta_j(ij) (Section II-B duplicated variables,
+ *     i = from bus, j = to bus).
+ */
+#ifndef ADMM_H
+#define ADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct admm_handle admm_handle;   /* opaque; owned by the library */
+
+enum {
+    ADMM_OK = 0,                 /* converged (or the requested work finished)     */
+    ADMM_NOT_CONVERGED = 1,      /* iteration caps reached; state stays valid       */
+    ADMM_ERR_INVALID_ARG = -1,   /* rejected input; nothing changed                 */
+    ADMM_ERR_CUDA = -2,          /* a CUDA call failed; see admm_last_error()       */
+    ADMM_ERR_NUMERICAL = -3,     /* a residual became NaN/Inf; iteration stopped    */
+    ADMM_ERR_OOM = -4            /* device allocation failed                        */
+};
+
+/* Grid data (eq. acopf, Section II-A).  Every bus must have at least one
+ * incident branch; branches may not connect a bus to itself.  tap == 0 means 1.
+ * rate_a <= 0 means an unlimited line. */
+typedef struct {
+    int32_t nbus, nbranch, ngen, ref_bus;
+    double base_mva;
+    const double *pd, *qd, *gs, *bs, *vmin, *vmax;                   /* [nbus]    */
+    const int32_t *f_bus, *t_bus;                                    /* [nbranch] */
+    const double *r, *x, *b, *tap, *shift, *rate_a;                  /* [nbranch] */
+    const int32_t *gen_bus;                                          /* [ngen]    */
+    const double *pmin, *pmax, *qmin, *qmax, *c2, *c1, *c0;          /* [ngen]    */
+} admm_grid;
+
+/* Method parameters.  rho_pq / rho_va are the fixed penalties of Table 1
+ * (generation and flow couplings / voltage couplings), obj_scale the objective
+ * multiplier of Section IV-A, line_limit_frac the 99% tightening of
+ * Section IV-A, max_outer / max_inner the caps of Section IV-A.  The remaining
+ * constants are this library's readings of what the paper leaves open (outer
+ * update, line-limit augmented Lagrangian, TRON tolerances). */
+typedef struct {
+    double rho_pq, rho_va, obj_scale, line_limit_frac;
+    double beta0;          /* initial outer penalty; <= 0 selects 10 rho_va        */
+    double beta_factor;    /* beta growth when ||z|| stalls (6)                      */
+    double z_decay;        /* ||z|| must fall below this fraction per outer step (0.8) */
+    double beta_max;       /* cap on beta (1e12)                                     */
+    double lambda_max;     /* projection bound of the outer multiplier (1e12)        */
+    double tol_in0;        /* inner tolerance at outer step k: max(tol, tol_in0 *    */
+    double tol_in_decay;   /*   tol_in_decay^k)  (0.1, 0.5)                          */
+    double al_rho0;        /* initial rho-tilde of a branch solve; <= 0: rho_pq     */
+    double al_tol;         /* line-limit AL stops when max|h| <= al_tol (1e-8)       */
+    double al_decay;       /* rho-tilde grows unless max|h| fell below this share (0.25) */
+    double al_rho_factor;  /* rho-tilde growth (10)                                  */
+    double al_rho_max;     /* cap on rho-tilde (1e12)                                */
+    double tron_gtol;      /* TRON: ||P(x-g)-x||_inf <= gtol max(1, start value) (1e-10) */
+    double tron_ftol;      /* TRON: model trusted below ftol max(1,|f|) (1e-12)     */
+    double tron_xtol;      /* TRON: stop on ||s||_inf <= xtol max(1, ||x||_inf) (1e-13) */
+    int32_t two_level;     /* 1: two-level algorithm; 0: z == 0 (one level)          */
+    int32_t max_outer, max_inner;   /* 20, 1000 (Section IV-A)                        */
+    int32_t al_max_iter;   /* 20 */
+    int32_t tron_max_iter; /* 200 */
+    int32_t use_graph;     /* 1: conditional-WHILE CUDA graph; 0: stream launches   */
+} admm_options;
+
+typedef struct {
+    int32_t iters;          /* inner iterations of the last solve                    */
+    int32_t outer_iters;    /* outer updates of the last solve                       */
+    int32_t status;         /* return code of the last solve                         */
+    int32_t tron_failures;  /* TRON solves that hit tron_max_iter in the last solve  */
+    double primal_res;      /* ||u - xbar||_2 over all couplings (last iteration)    */
+    double dual_res;        /* ||rho (xbar - xbar_prev)||_2                          */
+    double z_norm;          /* ||z||_2                                               */
+    double primal_z;        /* ||u - xbar + z||_2 (inner residual)                   */
+    double beta;            /* current outer penalty                                 */
+    double objective;       /* generation cost at the last admm_get_solution        */
+    double max_viol;        /* ||c(x)||_inf at the last admm_get_solution           */
+} admm_residuals;
+
+/* Fill *o with the defaults listed above (rho_pq 10, rho_va 1e3, Table 1). */
+void admm_default_options(admm_options *o);
+
+/* Validate the grid, compute the pi-model admittances (Section II-A), build
+ * the bus->incident-component CSR map (rows: branch ends in increasing branch
+ * id, from-end first, then generators in increasing id), allocate the device
+ * state on the current device and cold-start it (Section IV-B).
+ * o == NULL selects the defaults.  On success *out owns the handle. */
+int admm_create(const admm_grid *g, const admm_options *o, admm_handle **out);
+void admm_destroy(admm_handle *h);
+
+/* Run all device work of this handle on the given cudaStream_t (NULL: the
+ * legacy default stream).  The stream must outlive its use by the handle. */
+int admm_set_stream(admm_handle *h, void *cuda_stream);
+
+/* Replace the bus loads (host arrays [nbus]) -- the tracking input of
+ * Section IV-C.  admm_set_loads_device takes device pointers instead; both are
+ * ordered on the handle's stream. */
+int admm_set_loads(admm_handle *h, const double *pd, const double *qd);
+int admm_set_loads_device(admm_handle *h, const double *d_pd, const double *d_qd);
+
+/* Replace the generator real-power bounds (host arrays [ngen]), e.g. ramp
+ * limits around the previous dispatch when tracking (Section IV-C). */
+int admm_set_gen_bounds(admm_handle *h, const double *pmin, const double *pmax);
+
+/* Algorithm 1.  warm_start = 0 re-initialises every variable (Section IV-B);
+ * 1 keeps all primal, dual and penalty values (Section IV-C) and restarts only
+ * the loop counters.  Stops with ADMM_OK when ||u - xbar||, ||rho dxbar|| and
+ * ||z|| (two-level only) are all <= tol, else with ADMM_NOT_CONVERGED after
+ * max_iter inner iterations or max_outer outer updates.  Blocks until done. */
+int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
+               int32_t warm_start);
+/* Same, without waiting: the work is enqueued on the handle's stream; read the
+ * outcome with admm_get_residuals after synchronising that stream. */
+int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
+                     int32_t warm_start);
+
+/* Section IV-A solution: pg, qg [ngen] from the generator subproblems, vm, va
+ * [nbus] from the bus subproblems (vm = sqrt(w)), branch flows pf, qf, pt, qt
+ * [nbranch] recomputed from the bus voltages.  Any pointer may be NULL.  Also
+ * computes the objective and ||c(x)||_inf reported by admm_get_residuals. */
+int admm_get_solution(admm_handle *h, double *pg, double *qg, double *vm, double *va, double *pf,
+                      double *qf, double *pt, double *qt);
+int admm_get_residuals(admm_handle *h, admm_residuals *out);
+
+/* Per-iteration residual history of the last solve: rows of 4 doubles
+ * (primal, dual, z_norm, primal_z); returns the number of rows written
+ * (at most cap; the device keeps the last 65536 iterations). */
+int32_t admm_get_history(admm_handle *h, double *out, int32_t cap);
+
+/* Copy one state vector to a host buffer, in canonical order:
+ *   ADMM_VEC_U, _XBAR, _Z, _Y, _LAMBDA, _RHO : [m] per coupling
+ *   ADMM_VEC_BRANCH_X  : [nbranch][6] v_i, v_j, theta_i(ij), theta_j(ij), s_ij, s_ji
+ *   ADMM_VEC_BRANCH_LT : [nbranch][2] lambda-tilde of the two line-limit rows
+ *   ADMM_VEC_BUS       : [nbus][2] w, theta
+ *   ADMM_VEC_ADMITTANCE: [nbranch][8] g_ii b_ii g_ij b_ij g_ji b_ji g_jj b_jj */
+enum { ADMM_VEC_U = 0, ADMM_VEC_XBAR = 1, ADMM_VEC_Z = 2, ADMM_VEC_Y = 3, ADMM_VEC_LAMBDA = 4,
+       ADMM_VEC_BRANCH_X = 5, ADMM_VEC_BRANCH_LT = 6, ADMM_VEC_BUS = 7, ADMM_VEC_RHO = 8,
+       ADMM_VEC_ADMITTANCE = 9 };
+int admm_get_vector(admm_handle *h, int32_t which, double *out);
+
+/* The CSR bus -> incident-component map: row_ptr [nbus+1], col [2 nbranch + ngen]
+ * with entry 2l (+1) the from (to) end of branch l and 2 nbranch + g generator g. */
+int admm_get_csr(admm_handle *h, int32_t *row_ptr, int32_t *col);
+
+/* Counters of the last solve (summed over branches): TRON calls, TRON
+ * iterations, gradient/Hessian evaluations, function evaluations, Cauchy
+ * trials, CG iterations, projected-search trials, AL passes, TRON cap hits. */
+int admm_get_stats(admm_handle *h, int64_t *out9);
+
+/* Checkpoint: the full iteration state as an opaque host blob.  Call with
+ * buf == NULL to get the size in *len.  admm_set_state accepts only a blob of
+ * the same grid shape; a following warm solve continues the saved trajectory. */
+int admm_get_state(admm_handle *h, void *buf, size_t *len);
+int admm_set_state(admm_handle *h, const void *buf, size_t len);
+
+/* Tracing: run `iters` inner iterations from the current state (warm, no
+ * convergence stop) with stream launches and CUDA events around each kernel on
+ * the handle's stream; ms_out[0] = mean branch_tron time, ms_out[1] = mean
+ * bus_dual time, ms_out[2] = mean time of one whole iteration, in ms.  Blocks. */
+int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out);
+
+const char *admm_status_string(int status);
+/* Text of the last error recorded by any call in this process (thread-local). */
+const char *admm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,99 @@
+// Internal device-side definitions of libadmm (not part of the public ABI).
+//
+// Device layout (structure of arrays, FP64 unless noted; nl branches, ng
+// generators, nb buses, ns = 2 nl + ng incidence slots in CSR order):
+//   branch params  Y[8][nl] (g_ii b_ii g_ij b_ij g_ji b_ji g_jj b_jj),
+//                  lim[5][nl] (vmin_i, vmax_i, vmin_j, vmax_j, s lower bound)
+//   branch state   bx[6][nl] (v_i v_j th_i th_j s_ij s_ji), blt[2][nl] (lambda-tilde)
+//   branch I/O     bt[8][nl] targets xbar - z - y/rho written by the bus kernel,
+//                  bu[8][nl] component-side coupling values written by branch_tron
+//   generators     gc[3][ng] (c2' c1' c0 per-unit costs), glim[4][ng], gu[2][ng]
+//   buses          bus[6][nb] (pd qd gs bs vmin vmax), bw[nb], bth[nb], row_ptr[nb+1]
+//   slots          col[ns] (int32 entry id), sx[2][ns] bus-side p/q copies,
+//                  sz, sy, sl [4][ns]: z, y, lambda of the slot's couplings
+//                  (p, q, w, theta for a branch end; p, q for a generator)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace admm {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kHistCap = 65536;      // residual history ring (rows of 4 doubles)
+constexpr int kNumStats = 9;
+
+// Counters of one solve, summed over branches.
+enum StatId { ST_TRON_CALLS = 0, ST_TRON_ITERS, ST_FGH, ST_F, ST_CAUCHY, ST_CG, ST_PS, ST_AL,
+              ST_TRON_MAXHIT };
+
+// Loop status kept on the device.
+enum { CS_RUNNING = 2 };
+
+struct Ctrl {
+    // per-solve inputs (written by the begin kernel)
+    double tol, rho_pq, rho_va;
+    int32_t max_iter, warm;
+    // loop state (Algorithm 1)
+    int32_t iter, inner, outer, status, done, pending, total_iters, pad0;
+    double beta, beta_used, tol_in, zprev;
+    double pri, dual, zn, pri_z;
+    // finalize outputs
+    double objective, max_viol;
+    unsigned int counter;          // last-block detection of bus_dual
+    unsigned int fin_counter;      // last-block detection of finalize
+    unsigned long long stats[kNumStats];
+};
+
+struct DevOpts {
+    double obj_scale;
+    double beta0, beta_factor, z_decay, beta_max, lambda_max, tol_in0, tol_in_decay;
+    double al_rho0, al_tol, al_decay, al_rho_factor, al_rho_max;
+    double tron_gtol, tron_ftol, tron_xtol;
+    int32_t two_level, max_outer, max_inner, al_max_iter, tron_max_iter, pad;
+};
+
+struct DevGrid {
+    int32_t nb, nl, ng, ns, ref;
+    int32_t nblk_bus;              // blocks of the bus_dual launch
+    // branches
+    const int32_t *f_bus, *t_bus;
+    double *Y, *lim, *bx, *blt, *bt, *bu;
+    const double *raw;             // r x b tap shift rate [6][nl] for the admittance kernel
+    // generators
+    const int32_t *gen_bus;
+    double *gc, *glim, *gu;
+    // buses
+    double *bus, *bw, *bth;
+    const int32_t *row_ptr, *col;
+    // slots
+    double *sx, *sz, *sy, *sl;
+    // scratch and control
+    double *partials;              // [nblk_bus][4]
+    double *fin_partials;          // [nblk_fin][2]
+    double *hist;                  // [kHistCap][4]
+    Ctrl *ctrl;
+    double line_limit_frac;
+};
+
+struct SolveParams {
+    double tol, rho_pq, rho_va;
+    int32_t max_iter, warm;
+};
+
+// kernels
+__global__ void admittance_kernel(DevGrid G);
+__global__ void cold_start_kernel(DevGrid G, double beta_init);
+__global__ void begin_kernel(DevGrid G, DevOpts O, SolveParams P);
+__global__ void branch_tron_kernel(DevGrid G, DevOpts O);
+__global__ void bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond,
+                                int32_t use_cond);
+__global__ void flush_lambda_kernel(DevGrid G, DevOpts O);
+__global__ void finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va,
+                                double *pf, double *qf, double *pt, double *qt, int32_t nblk);
+
+constexpr int kBranchBlock = 128;
+constexpr int kBusBlock = 256;
+constexpr int kFinBlock = 256;
+
+}  // namespace admm

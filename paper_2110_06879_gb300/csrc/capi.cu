@@ -1,0 +1,807 @@
+// C ABI of libadmm (include/admm.h): handle life cycle, host-side setup
+// (validation, CSR incidence map), device allocation, the iteration graph and
+// the copy-out of results.  All numerical work runs in the kernels of
+// branch_tron.cu and bus_dual.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/admm.h"
+#include "admm_internal.cuh"
+
+using namespace admm;
+
+namespace {
+
+thread_local std::string g_err;
+
+void set_err(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                       \
+            return e_ == cudaErrorMemoryAllocation ? ADMM_ERR_OOM : ADMM_ERR_CUDA;   \
+        }                                                                            \
+    } while (0)
+
+constexpr uint64_t kStateMagic = 0x41444d4d53543031ull;   // "ADMMST01"
+
+}  // namespace
+
+struct admm_handle {
+    int32_t nb = 0, nl = 0, ng = 0, ns = 0, ref = 0;
+    double base = 100.0;
+    admm_options opts{};
+    DevGrid G{};
+    DevOpts O{};
+    cudaStream_t stream = nullptr;
+    void *dmem = nullptr;        // one device allocation, carved into the arrays
+    size_t dbytes = 0;
+    double *dout = nullptr;      // finalize outputs [2 nb + 4 nl + 2 ng]
+    Ctrl *hctrl = nullptr;       // pinned host mirror of the device control block
+    std::vector<int32_t> row_ptr, col, f_bus, t_bus, gen_bus;
+    int nblk_branch = 0, nblk_bus = 0, nblk_cold = 0, nblk_fin = 0, nblk_flush = 0;
+    // iteration graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t begin_node = nullptr;
+    SolveParams begin_params{};
+    void *begin_args[3] = {nullptr, nullptr, nullptr};
+    bool graph_ok = false;
+    int last_status = ADMM_OK;
+    double last_obj = 0.0, last_viol = 0.0;
+};
+
+extern "C" void admm_default_options(admm_options *o)
+{
+    std::memset(o, 0, sizeof(*o));
+    o->rho_pq = 10.0;
+    o->rho_va = 1000.0;
+    o->obj_scale = 1.0;
+    o->line_limit_frac = 0.99;
+    o->beta0 = 0.0;
+    o->beta_factor = 6.0;
+    o->z_decay = 0.8;
+    o->beta_max = 1e12;
+    o->lambda_max = 1e12;
+    o->tol_in0 = 0.1;
+    o->tol_in_decay = 0.5;
+    o->al_rho0 = 0.0;
+    o->al_tol = 1e-8;
+    o->al_decay = 0.25;
+    o->al_rho_factor = 10.0;
+    o->al_rho_max = 1e12;
+    o->tron_gtol = 1e-10;
+    o->tron_ftol = 1e-12;
+    o->tron_xtol = 1e-13;
+    o->two_level = 1;
+    o->max_outer = 20;
+    o->max_inner = 1000;
+    o->al_max_iter = 20;
+    o->tron_max_iter = 200;
+    o->use_graph = 1;
+}
+
+extern "C" const char *admm_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *admm_status_string(int s)
+{
+    switch (s) {
+    case ADMM_OK: return "ADMM_OK";
+    case ADMM_NOT_CONVERGED: return "ADMM_NOT_CONVERGED";
+    case ADMM_ERR_INVALID_ARG: return "ADMM_ERR_INVALID_ARG";
+    case ADMM_ERR_CUDA: return "ADMM_ERR_CUDA";
+    case ADMM_ERR_NUMERICAL: return "ADMM_ERR_NUMERICAL";
+    case ADMM_ERR_OOM: return "ADMM_ERR_OOM";
+    default: return "ADMM_UNKNOWN_STATUS";
+    }
+}
+
+namespace {
+
+bool finite_all(const double *a, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+int validate(const admm_grid *g, const admm_options *o)
+{
+    if (!g) { set_err("grid is NULL"); return ADMM_ERR_INVALID_ARG; }
+    if (g->nbus < 1 || g->nbranch < 1 || g->ngen < 0) {
+        set_err("need nbus >= 1, nbranch >= 1, ngen >= 0");
+        return ADMM_ERR_INVALID_ARG;
+    }
+    long long ns = 2LL * g->nbranch + g->ngen, m = 2LL * g->ngen + 8LL * g->nbranch;
+    if (m > 0x7fffffffLL || ns > 0x7fffffffLL) { set_err("grid too large"); return ADMM_ERR_INVALID_ARG; }
+    if (g->ref_bus < 0 || g->ref_bus >= g->nbus) { set_err("ref_bus out of range"); return ADMM_ERR_INVALID_ARG; }
+    if (!(g->base_mva > 0.0)) { set_err("base_mva must be positive"); return ADMM_ERR_INVALID_ARG; }
+    const double *bus_arrays[] = {g->pd, g->qd, g->gs, g->bs, g->vmin, g->vmax};
+    const double *br_arrays[] = {g->r, g->x, g->b, g->tap, g->shift, g->rate_a};
+    const double *gen_arrays[] = {g->pmin, g->pmax, g->qmin, g->qmax, g->c2, g->c1, g->c0};
+    for (auto a : bus_arrays)
+        if (!a || !finite_all(a, g->nbus)) { set_err("bus array NULL or not finite"); return ADMM_ERR_INVALID_ARG; }
+    for (auto a : br_arrays)
+        if (!a || !finite_all(a, g->nbranch)) { set_err("branch array NULL or not finite"); return ADMM_ERR_INVALID_ARG; }
+    if (g->ngen > 0) {
+        for (auto a : gen_arrays)
+            if (!a || !finite_all(a, g->ngen)) { set_err("generator array NULL or not finite"); return ADMM_ERR_INVALID_ARG; }
+        if (!g->gen_bus) { set_err("gen_bus is NULL"); return ADMM_ERR_INVALID_ARG; }
+    }
+    if (!g->f_bus || !g->t_bus) { set_err("f_bus/t_bus NULL"); return ADMM_ERR_INVALID_ARG; }
+    std::vector<int> deg(g->nbus, 0);
+    for (int l = 0; l < g->nbranch; ++l) {
+        int f = g->f_bus[l], t = g->t_bus[l];
+        if (f < 0 || f >= g->nbus || t < 0 || t >= g->nbus) { set_err("branch %d: bus index out of range", l); return ADMM_ERR_INVALID_ARG; }
+        if (f == t) { set_err("branch %d connects bus %d to itself", l, f); return ADMM_ERR_INVALID_ARG; }
+        if (g->r[l] == 0.0 && g->x[l] == 0.0) { set_err("branch %d has zero impedance", l); return ADMM_ERR_INVALID_ARG; }
+        deg[f]++; deg[t]++;
+    }
+    for (int i = 0; i < g->nbus; ++i) {
+        if (deg[i] == 0) { set_err("bus %d has no incident branch", i); return ADMM_ERR_INVALID_ARG; }
+        if (!(g->vmin[i] > 0.0) || g->vmin[i] > g->vmax[i]) { set_err("bus %d: need 0 < vmin <= vmax", i); return ADMM_ERR_INVALID_ARG; }
+    }
+    for (int k = 0; k < g->ngen; ++k) {
+        if (g->gen_bus[k] < 0 || g->gen_bus[k] >= g->nbus) { set_err("generator %d: bus out of range", k); return ADMM_ERR_INVALID_ARG; }
+        if (g->pmin[k] > g->pmax[k] || g->qmin[k] > g->qmax[k]) { set_err("generator %d: empty bounds", k); return ADMM_ERR_INVALID_ARG; }
+        if (g->c2[k] < 0.0) { set_err("generator %d: negative quadratic cost", k); return ADMM_ERR_INVALID_ARG; }
+    }
+    if (o) {
+        if (!(o->rho_pq > 0.0) || !(o->rho_va > 0.0)) { set_err("penalties must be positive"); return ADMM_ERR_INVALID_ARG; }
+        if (o->max_outer < 1 || o->max_inner < 1 || o->tron_max_iter < 1 || o->al_max_iter < 1) {
+            set_err("iteration caps must be >= 1");
+            return ADMM_ERR_INVALID_ARG;
+        }
+    }
+    return ADMM_OK;
+}
+
+// carve 256-byte aligned sub-buffers out of one allocation
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t n)
+    {
+        size_t o = off;
+        off += ((n * sizeof(T) + 255) / 256) * 256;
+        return o;
+    }
+};
+
+int launch_check(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_err("%s launch failed: %s", what, cudaGetErrorString(e));
+        return ADMM_ERR_CUDA;
+    }
+    return ADMM_OK;
+}
+
+int build_graph(admm_handle *h)
+{
+    cudaGraph_t graph;
+    CK(cudaGraphCreate(&graph, 0));
+    h->graph = graph;
+    // begin node (per-solve parameters are updated in the executable graph)
+    h->begin_args[0] = &h->G;
+    h->begin_args[1] = &h->O;
+    h->begin_args[2] = &h->begin_params;
+    cudaKernelNodeParams kp{};
+    kp.func = (void *)begin_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = h->begin_args;
+    CK(cudaGraphAddKernelNode(&h->begin_node, graph, nullptr, 0, &kp));
+    // WHILE node over one iteration
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, graph, &h->begin_node, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    void *bargs[2] = {&h->G, &h->O};
+    cudaKernelNodeParams bp{};
+    bp.func = (void *)branch_tron_kernel;
+    bp.gridDim = dim3(h->nblk_branch);
+    bp.blockDim = dim3(kBranchBlock);
+    bp.kernelParams = bargs;
+    cudaGraphNode_t bnode, unode, fnode;
+    CK(cudaGraphAddKernelNode(&bnode, body, nullptr, 0, &bp));
+    int32_t use_cond = 1;
+    void *uargs[4] = {&h->G, &h->O, &cond, &use_cond};
+    cudaKernelNodeParams up{};
+    up.func = (void *)bus_dual_kernel;
+    up.gridDim = dim3(h->nblk_bus);
+    up.blockDim = dim3(kBusBlock);
+    up.kernelParams = uargs;
+    CK(cudaGraphAddKernelNode(&unode, body, &bnode, 1, &up));
+    void *fargs[2] = {&h->G, &h->O};
+    cudaKernelNodeParams fp{};
+    fp.func = (void *)flush_lambda_kernel;
+    fp.gridDim = dim3(h->nblk_flush);
+    fp.blockDim = dim3(256);
+    fp.kernelParams = fargs;
+    CK(cudaGraphAddKernelNode(&fnode, graph, &wnode, 1, &fp));
+    CK(cudaGraphInstantiate(&h->exec, graph, 0));
+    h->graph_ok = true;
+    return ADMM_OK;
+}
+
+void destroy_graph(admm_handle *h)
+{
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->graph_ok = false;
+}
+
+int cold_start(admm_handle *h)
+{
+    double beta_init = h->opts.beta0 > 0.0 ? h->opts.beta0 : 10.0 * h->opts.rho_va;
+    cold_start_kernel<<<h->nblk_cold, 256, 0, h->stream>>>(h->G, beta_init);
+    return launch_check("cold_start_kernel");
+}
+
+}  // namespace
+
+extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handle **out)
+{
+    if (!out) { set_err("out is NULL"); return ADMM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    int rc = validate(g, o);
+    if (rc != ADMM_OK) return rc;
+    admm_handle *h = new admm_handle();
+    if (o) h->opts = *o; else admm_default_options(&h->opts);
+    const admm_options &op = h->opts;
+    h->nb = g->nbus; h->nl = g->nbranch; h->ng = g->ngen; h->ref = g->ref_bus;
+    h->ns = 2 * h->nl + h->ng;
+    h->base = g->base_mva;
+    const int nb = h->nb, nl = h->nl, ng = h->ng, ns = h->ns;
+    // CSR bus -> incident entries by a stable counting sort over entry ids
+    h->f_bus.assign(g->f_bus, g->f_bus + nl);
+    h->t_bus.assign(g->t_bus, g->t_bus + nl);
+    h->gen_bus.assign(g->gen_bus ? g->gen_bus : nullptr, g->gen_bus ? g->gen_bus + ng : nullptr);
+    h->row_ptr.assign(nb + 1, 0);
+    h->col.assign(ns, 0);
+    auto bus_of = [&](int e) { return e < 2 * nl ? ((e & 1) ? h->t_bus[e >> 1] : h->f_bus[e >> 1]) : h->gen_bus[e - 2 * nl]; };
+    for (int e = 0; e < ns; ++e) h->row_ptr[bus_of(e) + 1]++;
+    for (int i = 0; i < nb; ++i) h->row_ptr[i + 1] += h->row_ptr[i];
+    {
+        std::vector<int32_t> fill(h->row_ptr.begin(), h->row_ptr.end() - 1);
+        for (int e = 0; e < ns; ++e) h->col[fill[bus_of(e)]++] = e;
+    }
+    h->nblk_branch = (nl + kBranchBlock - 1) / kBranchBlock;
+    h->nblk_bus = (nb + kBusBlock - 1) / kBusBlock;
+    h->nblk_cold = (nl + ns + nb + ng + 1 + 255) / 256;
+    h->nblk_fin = (nb + nl + ng + kFinBlock - 1) / kFinBlock;
+    h->nblk_flush = (4 * ns + 255) / 256 < 1184 ? (4 * ns + 255) / 256 : 1184;
+    // device layout
+    Carver cv;
+    size_t o_fb = cv.take<int32_t>(nl), o_tb = cv.take<int32_t>(nl);
+    size_t o_Y = cv.take<double>(8 * (size_t)nl), o_lim = cv.take<double>(5 * (size_t)nl);
+    size_t o_bx = cv.take<double>(6 * (size_t)nl), o_blt = cv.take<double>(2 * (size_t)nl);
+    size_t o_bt = cv.take<double>(8 * (size_t)nl), o_bu = cv.take<double>(8 * (size_t)nl);
+    size_t o_raw = cv.take<double>(6 * (size_t)nl);
+    size_t o_gb = cv.take<int32_t>(ng > 0 ? ng : 1);
+    size_t o_gc = cv.take<double>(3 * (size_t)ng + 1), o_glim = cv.take<double>(4 * (size_t)ng + 1);
+    size_t o_gu = cv.take<double>(2 * (size_t)ng + 1);
+    size_t o_bus = cv.take<double>(6 * (size_t)nb), o_bw = cv.take<double>(nb), o_bth = cv.take<double>(nb);
+    size_t o_rp = cv.take<int32_t>(nb + 1), o_col = cv.take<int32_t>(ns);
+    size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
+    size_t o_sy = cv.take<double>(4 * (size_t)ns), o_sl = cv.take<double>(4 * (size_t)ns);
+    size_t o_part = cv.take<double>(4 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
+    size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
+    size_t o_ctrl = cv.take<Ctrl>(1);
+    size_t o_out = cv.take<double>(2 * (size_t)nb + 4 * (size_t)nl + 2 * (size_t)ng + 1);
+    h->dbytes = cv.off;
+    cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
+    if (e != cudaSuccess) {
+        set_err("cudaMalloc(%zu) failed: %s", h->dbytes, cudaGetErrorString(e));
+        delete h;
+        return e == cudaErrorMemoryAllocation ? ADMM_ERR_OOM : ADMM_ERR_CUDA;
+    }
+    e = cudaMallocHost(&h->hctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) {
+        set_err("cudaMallocHost failed: %s", cudaGetErrorString(e));
+        cudaFree(h->dmem);
+        delete h;
+        return ADMM_ERR_CUDA;
+    }
+    char *base = (char *)h->dmem;
+    DevGrid &G = h->G;
+    G.nb = nb; G.nl = nl; G.ng = ng; G.ns = ns; G.ref = h->ref;
+    G.nblk_bus = h->nblk_bus;
+    G.f_bus = (int32_t *)(base + o_fb); G.t_bus = (int32_t *)(base + o_tb);
+    G.Y = (double *)(base + o_Y); G.lim = (double *)(base + o_lim);
+    G.bx = (double *)(base + o_bx); G.blt = (double *)(base + o_blt);
+    G.bt = (double *)(base + o_bt); G.bu = (double *)(base + o_bu);
+    G.raw = (double *)(base + o_raw);
+    G.gen_bus = (int32_t *)(base + o_gb);
+    G.gc = (double *)(base + o_gc); G.glim = (double *)(base + o_glim); G.gu = (double *)(base + o_gu);
+    G.bus = (double *)(base + o_bus); G.bw = (double *)(base + o_bw); G.bth = (double *)(base + o_bth);
+    G.row_ptr = (int32_t *)(base + o_rp); G.col = (int32_t *)(base + o_col);
+    G.sx = (double *)(base + o_sx); G.sz = (double *)(base + o_sz);
+    G.sy = (double *)(base + o_sy); G.sl = (double *)(base + o_sl);
+    G.partials = (double *)(base + o_part); G.fin_partials = (double *)(base + o_fpart);
+    G.hist = (double *)(base + o_hist);
+    G.ctrl = (Ctrl *)(base + o_ctrl);
+    G.line_limit_frac = op.line_limit_frac;
+    h->dout = (double *)(base + o_out);
+    DevOpts &O = h->O;
+    O.obj_scale = op.obj_scale;
+    O.beta0 = op.beta0; O.beta_factor = op.beta_factor; O.z_decay = op.z_decay;
+    O.beta_max = op.beta_max; O.lambda_max = op.lambda_max;
+    O.tol_in0 = op.tol_in0; O.tol_in_decay = op.tol_in_decay;
+    O.al_rho0 = op.al_rho0; O.al_tol = op.al_tol; O.al_decay = op.al_decay;
+    O.al_rho_factor = op.al_rho_factor; O.al_rho_max = op.al_rho_max;
+    O.tron_gtol = op.tron_gtol; O.tron_ftol = op.tron_ftol; O.tron_xtol = op.tron_xtol;
+    O.two_level = op.two_level; O.max_outer = op.max_outer; O.max_inner = op.max_inner;
+    O.al_max_iter = op.al_max_iter; O.tron_max_iter = op.tron_max_iter;
+    // uploads (host staging in the device layout)
+    auto fail = [&](int code) { admm_destroy(h); return code; };
+    {
+        std::vector<double> bus(6 * (size_t)nb), raw(6 * (size_t)nl), gc(3 * (size_t)ng + 1), glim(4 * (size_t)ng + 1);
+        const double *ba[6] = {g->pd, g->qd, g->gs, g->bs, g->vmin, g->vmax};
+        for (int k = 0; k < 6; ++k) std::memcpy(&bus[(size_t)k * nb], ba[k], sizeof(double) * nb);
+        const double *ra[6] = {g->r, g->x, g->b, g->tap, g->shift, g->rate_a};
+        for (int k = 0; k < 6; ++k) std::memcpy(&raw[(size_t)k * nl], ra[k], sizeof(double) * nl);
+        for (int k = 0; k < ng; ++k) {
+            gc[k] = g->c2[k] * h->base * h->base;
+            gc[ng + k] = g->c1[k] * h->base;
+            gc[2 * ng + k] = g->c0[k];
+            glim[k] = g->pmin[k];
+            glim[ng + k] = g->pmax[k];
+            glim[2 * ng + k] = g->qmin[k];
+            glim[3 * ng + k] = g->qmax[k];
+        }
+        if (cudaMemset(h->dmem, 0, h->dbytes) != cudaSuccess ||
+            cudaMemcpy(G.bus, bus.data(), bus.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void *)G.raw, raw.data(), raw.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(G.gc, gc.data(), gc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(G.glim, glim.data(), glim.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void *)G.f_bus, g->f_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void *)G.t_bus, g->t_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            (ng > 0 && cudaMemcpy((void *)G.gen_bus, g->gen_bus, ng * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemcpy((void *)G.row_ptr, h->row_ptr.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy((void *)G.col, h->col.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_err("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(ADMM_ERR_CUDA);
+        }
+    }
+    admittance_kernel<<<(nl + 255) / 256, 256, 0, h->stream>>>(G);
+    if ((rc = launch_check("admittance_kernel")) != ADMM_OK) return fail(rc);
+    if ((rc = cold_start(h)) != ADMM_OK) return fail(rc);
+    if (op.use_graph) {
+        rc = build_graph(h);
+        if (rc != ADMM_OK) {
+            // fall back to stream launches (conditional graph nodes unavailable)
+            destroy_graph(h);
+            cudaGetLastError();
+            h->opts.use_graph = 0;
+        }
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(ADMM_ERR_CUDA);
+    }
+    *out = h;
+    return ADMM_OK;
+}
+
+extern "C" void admm_destroy(admm_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    destroy_graph(h);
+    if (h->dmem) cudaFree(h->dmem);
+    if (h->hctrl) cudaFreeHost(h->hctrl);
+    delete h;
+}
+
+extern "C" int admm_set_stream(admm_handle *h, void *s)
+{
+    if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
+    h->stream = (cudaStream_t)s;
+    return ADMM_OK;
+}
+
+extern "C" int admm_set_loads(admm_handle *h, const double *pd, const double *qd)
+{
+    if (!h || !pd || !qd) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    if (!finite_all(pd, h->nb) || !finite_all(qd, h->nb)) { set_err("loads not finite"); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->G.bus, pd, sizeof(double) * h->nb, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.bus + h->nb, qd, sizeof(double) * h->nb, cudaMemcpyHostToDevice, h->stream));
+    return ADMM_OK;
+}
+
+extern "C" int admm_set_loads_device(admm_handle *h, const double *d_pd, const double *d_qd)
+{
+    if (!h || !d_pd || !d_qd) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->G.bus, d_pd, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.bus + h->nb, d_qd, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, h->stream));
+    return ADMM_OK;
+}
+
+extern "C" int admm_set_gen_bounds(admm_handle *h, const double *pmin, const double *pmax)
+{
+    if (!h || !pmin || !pmax) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    for (int k = 0; k < h->ng; ++k)
+        if (!(pmin[k] <= pmax[k]) || !std::isfinite(pmin[k]) || !std::isfinite(pmax[k])) {
+            set_err("generator %d: empty or non-finite bounds", k);
+            return ADMM_ERR_INVALID_ARG;
+        }
+    if (h->ng == 0) return ADMM_OK;
+    CK(cudaMemcpyAsync(h->G.glim, pmin, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.glim + h->ng, pmax, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
+    return ADMM_OK;
+}
+
+extern "C" int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, double tol,
+                                int32_t max_iter, int32_t warm_start)
+{
+    if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
+    if (!(rho_pq > 0.0) || !(rho_va > 0.0) || !(tol >= 0.0) || max_iter < 0) {
+        set_err("need rho > 0, tol >= 0, max_iter >= 0");
+        return ADMM_ERR_INVALID_ARG;
+    }
+    h->opts.rho_pq = rho_pq;
+    h->opts.rho_va = rho_va;
+    int rc;
+    if (!warm_start && (rc = cold_start(h)) != ADMM_OK) return rc;
+    SolveParams sp{tol, rho_pq, rho_va, max_iter, warm_start};
+    if (max_iter == 0) {
+        begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
+        return launch_check("begin_kernel");
+    }
+    if (h->opts.use_graph && h->graph_ok) {
+        h->begin_params = sp;
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)begin_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = h->begin_args;
+        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->begin_node, &kp));
+        CK(cudaGraphLaunch(h->exec, h->stream));
+        return ADMM_OK;
+    }
+    begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
+    if ((rc = launch_check("begin_kernel")) != ADMM_OK) return rc;
+    cudaGraphConditionalHandle none = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
+        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O, none, 0);
+        if ((rc = launch_check("iteration kernels")) != ADMM_OK) return rc;
+        // poll the device flag now and then so a converged solve stops enqueuing
+        if ((it & 63) == 63) {
+            CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (h->hctrl->done) break;
+        }
+    }
+    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
+    return launch_check("flush_lambda_kernel");
+}
+
+extern "C" int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
+                          int32_t warm_start)
+{
+    int rc = admm_solve_async(h, rho_pq, rho_va, tol, max_iter, warm_start);
+    if (rc != ADMM_OK) return rc;
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int st = h->hctrl->status;
+    if (max_iter == 0) st = ADMM_NOT_CONVERGED;
+    h->last_status = st;
+    return st;
+}
+
+extern "C" int admm_get_residuals(admm_handle *h, admm_residuals *out)
+{
+    if (!h || !out) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const Ctrl &c = *h->hctrl;
+    out->iters = c.iter;
+    out->outer_iters = c.outer;
+    out->status = c.status == CS_RUNNING ? ADMM_NOT_CONVERGED : c.status;
+    out->tron_failures = (int32_t)c.stats[ST_TRON_MAXHIT];
+    out->primal_res = c.pri;
+    out->dual_res = c.dual;
+    out->z_norm = c.zn;
+    out->primal_z = c.pri_z;
+    out->beta = c.beta;
+    out->objective = h->last_obj;
+    out->max_viol = h->last_viol;
+    return ADMM_OK;
+}
+
+extern "C" int admm_get_solution(admm_handle *h, double *pg, double *qg, double *vm, double *va,
+                                 double *pf, double *qf, double *pt, double *qt)
+{
+    if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
+    const int nb = h->nb, nl = h->nl, ng = h->ng;
+    double *d = h->dout;
+    double *dvm = d, *dva = d + nb, *dpf = d + 2 * nb, *dqf = dpf + nl, *dpt = dqf + nl,
+           *dqt = dpt + nl, *dpg = dqt + nl, *dqg = dpg + ng;
+    finalize_kernel<<<h->nblk_fin, kFinBlock, 0, h->stream>>>(h->G, dpg, dqg, dvm, dva, dpf, dqf,
+                                                              dpt, dqt, h->nblk_fin);
+    int rc = launch_check("finalize_kernel");
+    if (rc != ADMM_OK) return rc;
+    struct { double *host; const double *dev; int n; } cp[] = {
+        {pg, dpg, ng}, {qg, dqg, ng}, {vm, dvm, nb}, {va, dva, nb},
+        {pf, dpf, nl}, {qf, dqf, nl}, {pt, dpt, nl}, {qt, dqt, nl}};
+    for (auto &c : cp)
+        if (c.host && c.n > 0)
+            CK(cudaMemcpyAsync(c.host, c.dev, sizeof(double) * c.n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->last_obj = h->hctrl->objective;
+    h->last_viol = h->hctrl->max_viol;
+    return ADMM_OK;
+}
+
+extern "C" int32_t admm_get_history(admm_handle *h, double *out, int32_t cap)
+{
+    if (!h || !out || cap < 0) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    if (cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_err("history copy failed");
+        return ADMM_ERR_CUDA;
+    }
+    int n = h->hctrl->iter;
+    if (n > kHistCap) n = kHistCap;   // the ring keeps the last kHistCap rows
+    if (n > cap) n = cap;
+    std::vector<double> all(4 * (size_t)kHistCap);
+    if (cudaMemcpy(all.data(), h->G.hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_err("history copy failed");
+        return ADMM_ERR_CUDA;
+    }
+    int total = h->hctrl->iter;
+    int first = total > kHistCap ? total - kHistCap : 0;
+    for (int r = 0; r < n; ++r) {
+        int it = first + r;
+        std::memcpy(out + 4 * (size_t)r, &all[4 * (size_t)(it % kHistCap)], 4 * sizeof(double));
+    }
+    return n;
+}
+
+namespace {
+
+int fetch(admm_handle *h, const double *dev, size_t n, std::vector<double> &v)
+{
+    v.resize(n);
+    if (n == 0) return ADMM_OK;
+    CK(cudaMemcpyAsync(v.data(), dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return ADMM_OK;
+}
+
+}  // namespace
+
+extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
+{
+    if (!h || !out) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    const int nb = h->nb, nl = h->nl, ng = h->ng, ns = h->ns;
+    const size_t m = 2 * (size_t)ng + 8 * (size_t)nl;
+    std::vector<double> a, b, c, d;
+    int rc = ADMM_OK;
+    auto cb = [&](int l, int k) { return 2 * (size_t)ng + 8 * (size_t)l + k; };
+    auto sync = [&]() -> int { CK(cudaStreamSynchronize(h->stream)); return ADMM_OK; };
+    switch (which) {
+    case ADMM_VEC_U:
+        if ((rc = fetch(h, h->G.bu, 8 * (size_t)nl, a)) || (rc = fetch(h, h->G.gu, 2 * (size_t)ng, b)) || (rc = sync())) return rc;
+        for (int g = 0; g < ng; ++g) { out[2 * g] = b[g]; out[2 * g + 1] = b[ng + g]; }
+        for (int l = 0; l < nl; ++l)
+            for (int k = 0; k < 8; ++k) out[cb(l, k)] = a[(size_t)k * nl + l];
+        return ADMM_OK;
+    case ADMM_VEC_XBAR:
+    case ADMM_VEC_Z:
+    case ADMM_VEC_Y:
+    case ADMM_VEC_LAMBDA: {
+        const double *src = which == ADMM_VEC_Z ? h->G.sz : which == ADMM_VEC_Y ? h->G.sy : h->G.sl;
+        if (which == ADMM_VEC_XBAR) {
+            if ((rc = fetch(h, h->G.sx, 2 * (size_t)ns, a)) || (rc = fetch(h, h->G.bw, nb, b)) ||
+                (rc = fetch(h, h->G.bth, nb, c)) || (rc = sync()))
+                return rc;
+        } else if ((rc = fetch(h, src, 4 * (size_t)ns, a)) || (rc = sync())) {
+            return rc;
+        }
+        for (int i = 0; i < nb; ++i) {
+            for (int k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) {
+                int e = h->col[k];
+                if (e < 2 * nl) {
+                    int l = e >> 1, end = e & 1;
+                    size_t cp = cb(l, end ? 2 : 0), cq = cb(l, end ? 3 : 1);
+                    size_t cw = cb(l, end ? 6 : 4), ct = cb(l, end ? 7 : 5);
+                    if (which == ADMM_VEC_XBAR) {
+                        out[cp] = a[k]; out[cq] = a[ns + k]; out[cw] = b[i]; out[ct] = c[i];
+                    } else {
+                        out[cp] = a[k]; out[cq] = a[ns + k]; out[cw] = a[2 * (size_t)ns + k];
+                        out[ct] = a[3 * (size_t)ns + k];
+                    }
+                } else {
+                    int g = e - 2 * nl;
+                    out[2 * g] = a[k];
+                    out[2 * g + 1] = a[ns + k];
+                }
+            }
+        }
+        return ADMM_OK;
+    }
+    case ADMM_VEC_RHO:
+        for (int g = 0; g < ng; ++g) { out[2 * g] = h->opts.rho_pq; out[2 * g + 1] = h->opts.rho_pq; }
+        for (int l = 0; l < nl; ++l)
+            for (int k = 0; k < 8; ++k) out[cb(l, k)] = k < 4 ? h->opts.rho_pq : h->opts.rho_va;
+        (void)m;
+        return ADMM_OK;
+    case ADMM_VEC_BRANCH_X:
+    case ADMM_VEC_BRANCH_LT:
+    case ADMM_VEC_ADMITTANCE: {
+        int w = which == ADMM_VEC_BRANCH_X ? 6 : which == ADMM_VEC_BRANCH_LT ? 2 : 8;
+        const double *src = which == ADMM_VEC_BRANCH_X ? h->G.bx : which == ADMM_VEC_BRANCH_LT ? h->G.blt : h->G.Y;
+        if ((rc = fetch(h, src, (size_t)w * nl, a)) || (rc = sync())) return rc;
+        for (int l = 0; l < nl; ++l)
+            for (int k = 0; k < w; ++k) out[(size_t)l * w + k] = a[(size_t)k * nl + l];
+        return ADMM_OK;
+    }
+    case ADMM_VEC_BUS:
+        if ((rc = fetch(h, h->G.bw, nb, a)) || (rc = fetch(h, h->G.bth, nb, b)) || (rc = sync())) return rc;
+        for (int i = 0; i < nb; ++i) { out[2 * i] = a[i]; out[2 * i + 1] = b[i]; }
+        return ADMM_OK;
+    default:
+        set_err("unknown vector id %d", which);
+        return ADMM_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" int admm_get_csr(admm_handle *h, int32_t *row_ptr, int32_t *col)
+{
+    if (!h || !row_ptr || !col) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    std::memcpy(row_ptr, h->row_ptr.data(), sizeof(int32_t) * (h->nb + 1));
+    std::memcpy(col, h->col.data(), sizeof(int32_t) * h->ns);
+    return ADMM_OK;
+}
+
+extern "C" int admm_get_stats(admm_handle *h, int64_t *out9)
+{
+    if (!h || !out9) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < kNumStats; ++k) out9[k] = (int64_t)h->hctrl->stats[k];
+    return ADMM_OK;
+}
+
+namespace {
+
+// state arrays of a handle, in blob order
+struct StatePart {
+    double *dev;
+    size_t n;
+};
+
+std::vector<StatePart> state_parts(admm_handle *h)
+{
+    const size_t nl = h->nl, ng = h->ng, nb = h->nb, ns = h->ns;
+    return {{h->G.bx, 6 * nl}, {h->G.blt, 2 * nl}, {h->G.bt, 8 * nl}, {h->G.bu, 8 * nl},
+            {h->G.gu, 2 * ng}, {h->G.bw, nb},      {h->G.bth, nb},    {h->G.sx, 2 * ns},
+            {h->G.sz, 4 * ns}, {h->G.sy, 4 * ns},  {h->G.sl, 4 * ns}};
+}
+
+}  // namespace
+
+extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
+{
+    if (!h || !len) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    auto parts = state_parts(h);
+    size_t n = 0;
+    for (auto &p : parts) n += p.n;
+    const size_t need = 4 * sizeof(uint64_t) + 4 * sizeof(double) + n * sizeof(double);
+    if (!buf) { *len = need; return ADMM_OK; }
+    if (*len < need) { set_err("state buffer too small (%zu < %zu)", *len, need); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    uint64_t *hdr = (uint64_t *)buf;
+    hdr[0] = kStateMagic; hdr[1] = (uint64_t)h->nb; hdr[2] = (uint64_t)h->nl; hdr[3] = (uint64_t)h->ng;
+    double *sc = (double *)(hdr + 4);
+    sc[0] = h->hctrl->beta;
+    sc[1] = (double)h->hctrl->total_iters;
+    sc[2] = h->hctrl->pending ? h->hctrl->beta_used : 0.0;
+    sc[3] = (double)h->hctrl->pending;
+    double *p = sc + 4;
+    for (auto &pt : parts) {
+        if (pt.n) CK(cudaMemcpyAsync(p, pt.dev, pt.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        p += pt.n;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return ADMM_OK;
+}
+
+extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
+{
+    if (!h || !buf) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
+    auto parts = state_parts(h);
+    size_t n = 0;
+    for (auto &p : parts) n += p.n;
+    const size_t need = 4 * sizeof(uint64_t) + 4 * sizeof(double) + n * sizeof(double);
+    const uint64_t *hdr = (const uint64_t *)buf;
+    if (len != need || hdr[0] != kStateMagic || hdr[1] != (uint64_t)h->nb || hdr[2] != (uint64_t)h->nl ||
+        hdr[3] != (uint64_t)h->ng) {
+        set_err("state blob does not match this grid");
+        return ADMM_ERR_INVALID_ARG;
+    }
+    const double *sc = (const double *)(hdr + 4);
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->hctrl->beta = sc[0];
+    h->hctrl->total_iters = (int32_t)sc[1];
+    h->hctrl->beta_used = sc[2];
+    h->hctrl->pending = (int32_t)sc[3];
+    h->hctrl->done = 0;
+    const double *p = sc + 4;
+    for (auto &pt : parts) {
+        if (pt.n) CK(cudaMemcpyAsync(pt.dev, p, pt.n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        p += pt.n;
+    }
+    CK(cudaMemcpyAsync(h->G.ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADMM_OK;
+}
+
+extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out)
+{
+    if (!h || !ms_out || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    SolveParams sp{0.0, h->opts.rho_pq, h->opts.rho_va, iters, 1};
+    begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
+    int rc = launch_check("begin_kernel");
+    if (rc != ADMM_OK) return rc;
+    std::vector<cudaEvent_t> ev(2 * (size_t)iters + 1);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    cudaGraphConditionalHandle none = 0;
+    CK(cudaEventRecord(ev[0], h->stream));
+    for (int it = 0; it < iters; ++it) {
+        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
+        CK(cudaEventRecord(ev[2 * it + 1], h->stream));
+        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O, none, 0);
+        CK(cudaEventRecord(ev[2 * it + 2], h->stream));
+    }
+    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
+    if ((rc = launch_check("profiled iteration")) != ADMM_OK) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    double tb = 0.0, tu = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, ev[2 * it], ev[2 * it + 1]));
+        CK(cudaEventElapsedTime(&b, ev[2 * it + 1], ev[2 * it + 2]));
+        tb += a;
+        tu += b;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    ms_out[0] = tb / iters;
+    ms_out[1] = tu / iters;
+    ms_out[2] = (tb + tu) / iters;
+    return ADMM_OK;
+}
