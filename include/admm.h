@@ -194,6 +194,36 @@ int admm_set_state(admm_handle *h, const void *buf, size_t len);
  * bus_dual time, ms_out[2] = mean time of one whole iteration, in ms.  Blocks. */
 int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out);
 
+/* Allocation-free z / y update (no counterpart in the paper; it serves
+ * callers).  Some callers cannot call cudaMalloc: a control loop whose device
+ * memory is fixed once at start-up, or a program whose device memory all
+ * belongs to another allocator and which must not let a library allocate
+ * behind its back.  This entry point runs the z update, the y update and the
+ * residual reduction of one inner iteration (lines 5-6 of Algorithm 1) on
+ * buffers the caller owns, and allocates nothing: its only scratch (per-block
+ * partial sums and a ticket counter) is a static device array of 128 KiB +
+ * 32 B that every GPU loading the library keeps until the process exits.
+ *   m                  couplings, 1 <= m <= 16,777,216 (larger m is rejected
+ *                      with ADMM_ERR_INVALID_ARG)
+ *   d_u, d_xbar        component-side values and bus-side copies [m]
+ *   d_xbar_prev        bus-side copies of the previous iteration [m]
+ *   d_rho, d_lambda    penalties and outer multipliers [m]
+ *   beta, two_level    outer penalty (>= 0); two_level = 0 keeps z at 0
+ *   d_z, d_y           in: previous z, y; out: updated z, y [m]
+ *   d_norms            out [4]: ||u - xbar||, ||u - xbar + z||,
+ *                      ||rho (xbar - xbar_prev)||, ||z|| (Euclidean)
+ *   cuda_stream        stream the work is ordered on (NULL: legacy stream)
+ * All d_ pointers are device pointers on the current device.  The first call
+ * on each device looks up the scratch array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one scratch array, so calls whose work overlaps on a GPU
+ * race: order them on one stream.  Returns ADMM_OK, ADMM_ERR_INVALID_ARG or
+ * ADMM_ERR_CUDA; the work is asynchronous. */
+int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
+                             const double *d_xbar_prev, const double *d_rho,
+                             const double *d_lambda, double beta, int32_t two_level,
+                             double *d_z, double *d_y, double *d_norms, void *cuda_stream);
+
 const char *admm_status_string(int status);
 /* Text of the last error recorded by any call in this process (thread-local). */
 const char *admm_last_error(void);

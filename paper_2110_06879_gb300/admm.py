@@ -80,6 +80,8 @@ def lib():
             "admm_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
             "admm_set_state": (C.c_int, [vp, vp, C.c_size_t]),
             "admm_profile_iterations": (C.c_int, [vp, i32, vp]),
+            "admm_dual_update_noalloc": (C.c_int, [C.c_int64, vp, vp, vp, vp, vp, d, i32, vp, vp,
+                                                   vp, vp]),
             "admm_status_string": (C.c_char_p, [C.c_int]),
             "admm_last_error": (C.c_char_p, []),
         }
