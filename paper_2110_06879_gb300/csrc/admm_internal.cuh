@@ -42,6 +42,8 @@ struct Ctrl {
     double objective, max_viol;
     unsigned int counter;          // last-block detection of bus_dual
     unsigned int fin_counter;      // last-block detection of finalize
+    unsigned int branch_next;      // work queue head of branch_tron (reset every iteration)
+    unsigned int pad1;
     unsigned long long stats[kNumStats];
 };
 
@@ -56,6 +58,8 @@ struct DevOpts {
 struct DevGrid {
     int32_t nb, nl, ng, ns, ref;
     int32_t nblk_bus;              // blocks of the bus_dual launch
+    int32_t nblk_branch;           // blocks of the (persistent) branch_tron launch
+    int32_t pad_;
     // branches
     const int32_t *f_bus, *t_bus;
     double *Y, *lim, *bx, *blt, *bt, *bu;
@@ -93,6 +97,7 @@ __global__ void finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, d
                                 double *pf, double *qf, double *pt, double *qt, int32_t nblk);
 
 constexpr int kBranchBlock = 128;
+constexpr int kBranchBlocksPerSM = 2;
 constexpr int kBusBlock = 256;
 constexpr int kFinBlock = 256;
 

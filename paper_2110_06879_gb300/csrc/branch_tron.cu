@@ -1,5 +1,5 @@
-// branch_tron: the branch x-update of Algorithm 1 (line 3) -- one thread per
-// branch solves eq. branch (Section II-C): minimise over
+// branch_tron: the branch x-update of Algorithm 1 (line 3).  Every branch
+// solves eq. branch (Section II-C): minimise over
 // x = (v_i, v_j, theta_i(ij), theta_j(ij), s_ij, s_ji) within bounds
 //   sum_c rho_c/2 (u_c(x) - t_c)^2 + sum_e [lt_e h_e + rt/2 h_e^2],
 //   h_e = p_e^2 + q_e^2 + s_e,
@@ -8,12 +8,21 @@
 // handled by an augmented Lagrangian loop around a trust-region Newton method
 // for bound constraints (Lin-More TRON with Steihaug CG, Section III-B).
 //
-// Everything lives in registers: the 6x6 Hessian is packed (21 entries), the
-// free-variable subspace of TRON is expressed with masks instead of index
-// compaction so every loop has a compile-time trip count, and one sincos per
-// function evaluation serves the four flows, their gradients and Hessians.
-// The FP64 pipe is the bound (GB300 FP64 is a small fraction of FP32), so the
-// code spends no FP64 work on anything that is not part of the method.
+// GB300 design.  FP64 runs at 2 FMA/clk/SM (about 1/58 of FP32), so the
+// kernel is bound by FP64 warp instructions, and a warp instruction costs the
+// same whether 32 lanes or 1 lane are active.  Branch problems need very
+// different amounts of work (1 to 20 AL passes, 1 to dozens of TRON
+// iterations), so one-branch-per-thread with a fixed assignment leaves most
+// lanes idle.  Instead the grid is persistent and every lane pulls a new branch
+// from a queue as soon as its branch is finished; each trip of the main loop
+// performs exactly one TRON iteration in every lane that has one to do, so the
+// expensive code runs with nearly full warps.  One lane solves one branch
+// entirely in registers (the Hessian packed, 21 entries; the TRON free set
+// handled with masks so all loops have fixed trip counts); the branch data the
+// evaluations read (admittances and targets) sit in shared memory.  The
+// function, gradient and Hessian are evaluated together at every trial point
+// (one sincos), since nearly every trial step is accepted; after a rejected
+// step the gradient and Hessian are re-evaluated at the kept point.
 #include "admm_internal.cuh"
 
 namespace admm {
@@ -22,44 +31,50 @@ namespace {
 constexpr double kMu0 = 0.01, kEta0 = 1e-3, kEta1 = 0.25, kEta2 = 0.75;
 constexpr double kSigma1 = 0.25, kSigma3 = 4.0, kCgRtol = 0.1;
 constexpr int kCauchyTrials = 20, kPsTrials = 20, kCgMaxit = 12, kCholTries = 20;
+constexpr unsigned kFull = 0xffffffffu;
 
-// packed symmetric index (i <= j or j <= i)
+// packed symmetric index
 __host__ __device__ constexpr int P(int i, int j)
 {
     return i <= j ? (i * (11 - i)) / 2 + j : (j * (11 - j)) / 2 + i;
 }
 
-struct Prob {
-    double Y[8];
-    double lo[6], hi[6];
-    double t[8];
-    double rpq, rva, lt0, lt1, rt;
-};
-
 struct Cnt {
     int tron_calls, tron_iters, fgh, f, cauchy, cg, ps, al, maxhit;
 };
 
+// bounds of one branch: v_i, v_j from the buses, theta copies +-2 pi, slacks
+struct Bounds {
+    double vlo_i, vhi_i, vlo_j, vhi_j, slo;
+    __device__ __forceinline__ double lo(int i) const
+    {
+        return i == 0 ? vlo_i : i == 1 ? vlo_j : i < 4 ? -kTwoPi : slo;
+    }
+    __device__ __forceinline__ double hi(int i) const
+    {
+        return i == 0 ? vhi_i : i == 1 ? vhi_j : i < 4 ? kTwoPi : 0.0;
+    }
+};
+
 __device__ __forceinline__ double clampd(double v, double lo, double hi)
 {
-    return v < lo ? lo : (v > hi ? hi : v);
+    return fmin(fmax(v, lo), hi);
 }
 
-// One flow a_self v_k^2 + v_i v_j (alpha cos th + beta sin th), its gradient in
-// (v_i, v_j, th) and Hessian entries (ii, jj, ij, i-th, j-th, th-th).
+// One flow a_self v_k^2 + v_i v_j (alpha cos th + beta sin th): value, gradient
+// in (v_i, v_j, th) and Hessian entries (ii, jj, ij, i-th, j-th, th-th).
 struct Flow {
     double F, d0, d1, d2, h00, h11, h01, h02, h12, h22;
 };
 
 template <bool kSelfI>
 __device__ __forceinline__ void flow(double a, double al, double be, double vi, double vj,
-                                     double vv, double c, double s, Flow &o, bool deriv)
+                                     double vv, double c, double s, Flow &o)
 {
-    double T = al * c + be * s;
-    double vk = kSelfI ? vi : vj;
+    const double T = al * c + be * s;
+    const double Tp = be * c - al * s;
+    const double vk = kSelfI ? vi : vj;
     o.F = a * vk * vk + vv * T;
-    if (!deriv) return;
-    double Tp = be * c - al * s;
     o.d0 = (kSelfI ? 2.0 * a * vi : 0.0) + vj * T;
     o.d1 = (kSelfI ? 0.0 : 2.0 * a * vj) + vi * T;
     o.d2 = vv * Tp;
@@ -71,51 +86,36 @@ __device__ __forceinline__ void flow(double a, double al, double be, double vi, 
     o.h22 = -vv * T;
 }
 
-__device__ __forceinline__ void flows4(const Prob &p, const double *x, Flow f[4], bool deriv)
+// f, gradient, packed Hessian and the four flows of eq. branch at x.
+// Y and t live in shared memory with stride kBranchBlock.
+__device__ __forceinline__ void evaluate(const double *sY, const double *sT, double rpq, double rva,
+                                         double lt0, double lt1, double rt, const double *x,
+                                         double &f, double *g, double *H, double *F)
 {
-    double vi = x[0], vj = x[1];
+    const double vi = x[0], vj = x[1];
     double s, c;
     sincos(x[2] - x[3], &s, &c);
-    double vv = vi * vj;
-    flow<true>(p.Y[0], p.Y[2], p.Y[3], vi, vj, vv, c, s, f[0], deriv);      // p_ij
-    flow<true>(-p.Y[1], -p.Y[3], p.Y[2], vi, vj, vv, c, s, f[1], deriv);    // q_ij
-    flow<false>(p.Y[6], p.Y[4], -p.Y[5], vi, vj, vv, c, s, f[2], deriv);    // p_ji
-    flow<false>(-p.Y[7], -p.Y[5], -p.Y[4], vi, vj, vv, c, s, f[3], deriv);  // q_ji
-}
-
-__device__ __forceinline__ double fval(const Prob &p, const double *x)
-{
+    const double vv = vi * vj;
+    constexpr int S = kBranchBlock;
+    const double gii = sY[0 * S], bii = sY[1 * S], gij = sY[2 * S], bij = sY[3 * S];
+    const double gji = sY[4 * S], bji = sY[5 * S], gjj = sY[6 * S], bjj = sY[7 * S];
     Flow fl[4];
-    flows4(p, x, fl, false);
-    double r0 = fl[0].F - p.t[0], r1 = fl[1].F - p.t[1], r2 = fl[2].F - p.t[2],
-           r3 = fl[3].F - p.t[3];
-    double rwi = x[0] * x[0] - p.t[4], rti = x[2] - p.t[5];
-    double rwj = x[1] * x[1] - p.t[6], rtj = x[3] - p.t[7];
-    double h0 = fl[0].F * fl[0].F + fl[1].F * fl[1].F + x[4];
-    double h1 = fl[2].F * fl[2].F + fl[3].F * fl[3].F + x[5];
-    double f = 0.5 * p.rpq * (r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3)
-             + 0.5 * p.rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj);
-    f += p.lt0 * h0 + 0.5 * p.rt * h0 * h0;
-    f += p.lt1 * h1 + 0.5 * p.rt * h1 * h1;
-    return f;
-}
-
-// gradient and packed Hessian (f not needed by callers)
-__device__ __forceinline__ void fgh(const Prob &p, const double *x, double *g, double *H)
-{
-    Flow fl[4];
-    flows4(p, x, fl, true);
-    double h0 = fl[0].F * fl[0].F + fl[1].F * fl[1].F + x[4];
-    double h1 = fl[2].F * fl[2].F + fl[3].F * fl[3].F + x[5];
-    double mu0 = p.lt0 + p.rt * h0, mu1 = p.lt1 + p.rt * h1;
-    double mu[4] = {mu0, mu0, mu1, mu1};
-    // coefficient of each flow gradient and of each flow Hessian
-    double G0 = 0.0, G1 = 0.0, G2 = 0.0;
+    flow<true>(gii, gij, bij, vi, vj, vv, c, s, fl[0]);      // p_ij eq. (pij)
+    flow<true>(-bii, -bij, gij, vi, vj, vv, c, s, fl[1]);    // q_ij eq. (qij)
+    flow<false>(gjj, gji, -bji, vi, vj, vv, c, s, fl[2]);    // p_ji eq. (pji)
+    flow<false>(-bjj, -bji, -gji, vi, vj, vv, c, s, fl[3]);  // q_ji eq. (qji)
+    const double h0 = fl[0].F * fl[0].F + fl[1].F * fl[1].F + x[4];
+    const double h1 = fl[2].F * fl[2].F + fl[3].F * fl[3].F + x[5];
+    const double mu0 = lt0 + rt * h0, mu1 = lt1 + rt * h1;
+    double G0 = 0.0, G1 = 0.0, G2 = 0.0, fq = 0.0;
     double A00 = 0.0, A11 = 0.0, A01 = 0.0, A02 = 0.0, A12 = 0.0, A22 = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        double ck = p.rpq * (fl[k].F - p.t[k]) + 2.0 * mu[k] * fl[k].F;
-        double wk = p.rpq + 2.0 * mu[k];
+        const double mu = k < 2 ? mu0 : mu1;
+        const double r = fl[k].F - sT[k * S];
+        fq += r * r;
+        const double ck = rpq * r + 2.0 * mu * fl[k].F;
+        const double wk = rpq + 2.0 * mu;
         G0 += ck * fl[k].d0;
         G1 += ck * fl[k].d1;
         G2 += ck * fl[k].d2;
@@ -125,45 +125,47 @@ __device__ __forceinline__ void fgh(const Prob &p, const double *x, double *g, d
         A02 += ck * fl[k].h02 + wk * fl[k].d0 * fl[k].d2;
         A12 += ck * fl[k].h12 + wk * fl[k].d1 * fl[k].d2;
         A22 += ck * fl[k].h22 + wk * fl[k].d2 * fl[k].d2;
+        F[k] = fl[k].F;
     }
     // gradients of h_e in (v_i, v_j, th)
-    double e00 = 2.0 * (fl[0].F * fl[0].d0 + fl[1].F * fl[1].d0);
-    double e01 = 2.0 * (fl[0].F * fl[0].d1 + fl[1].F * fl[1].d1);
-    double e02 = 2.0 * (fl[0].F * fl[0].d2 + fl[1].F * fl[1].d2);
-    double e10 = 2.0 * (fl[2].F * fl[2].d0 + fl[3].F * fl[3].d0);
-    double e11 = 2.0 * (fl[2].F * fl[2].d1 + fl[3].F * fl[3].d1);
-    double e12 = 2.0 * (fl[2].F * fl[2].d2 + fl[3].F * fl[3].d2);
-    const double rt = p.rt;
+    const double e00 = 2.0 * (fl[0].F * fl[0].d0 + fl[1].F * fl[1].d0);
+    const double e01 = 2.0 * (fl[0].F * fl[0].d1 + fl[1].F * fl[1].d1);
+    const double e02 = 2.0 * (fl[0].F * fl[0].d2 + fl[1].F * fl[1].d2);
+    const double e10 = 2.0 * (fl[2].F * fl[2].d0 + fl[3].F * fl[3].d0);
+    const double e11 = 2.0 * (fl[2].F * fl[2].d1 + fl[3].F * fl[3].d1);
+    const double e12 = 2.0 * (fl[2].F * fl[2].d2 + fl[3].F * fl[3].d2);
     A00 += rt * (e00 * e00 + e10 * e10);
     A11 += rt * (e01 * e01 + e11 * e11);
     A01 += rt * (e00 * e01 + e10 * e11);
     A02 += rt * (e00 * e02 + e10 * e12);
     A12 += rt * (e01 * e02 + e11 * e12);
     A22 += rt * (e02 * e02 + e12 * e12);
-    double vi = x[0], vj = x[1];
-    double rwi = vi * vi - p.t[4], rwj = vj * vj - p.t[6];
-    g[0] = G0 + p.rva * rwi * 2.0 * vi;
-    g[1] = G1 + p.rva * rwj * 2.0 * vj;
-    g[2] = G2 + p.rva * (x[2] - p.t[5]);
-    g[3] = -G2 + p.rva * (x[3] - p.t[7]);
+    const double rwi = vi * vi - sT[4 * S], rti = x[2] - sT[5 * S];
+    const double rwj = vj * vj - sT[6 * S], rtj = x[3] - sT[7 * S];
+    f = 0.5 * rpq * fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
+      + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
+    g[0] = G0 + 2.0 * rva * rwi * vi;
+    g[1] = G1 + 2.0 * rva * rwj * vj;
+    g[2] = G2 + rva * rti;
+    g[3] = -G2 + rva * rtj;
     g[4] = mu0;
     g[5] = mu1;
-    H[P(0, 0)] = A00 + p.rva * (4.0 * vi * vi + 2.0 * rwi);
+    H[P(0, 0)] = A00 + rva * (4.0 * vi * vi + 2.0 * rwi);
     H[P(0, 1)] = A01;
     H[P(0, 2)] = A02;
     H[P(0, 3)] = -A02;
     H[P(0, 4)] = rt * e00;
     H[P(0, 5)] = rt * e10;
-    H[P(1, 1)] = A11 + p.rva * (4.0 * vj * vj + 2.0 * rwj);
+    H[P(1, 1)] = A11 + rva * (4.0 * vj * vj + 2.0 * rwj);
     H[P(1, 2)] = A12;
     H[P(1, 3)] = -A12;
     H[P(1, 4)] = rt * e01;
     H[P(1, 5)] = rt * e11;
-    H[P(2, 2)] = A22 + p.rva;
+    H[P(2, 2)] = A22 + rva;
     H[P(2, 3)] = -A22;
     H[P(2, 4)] = rt * e02;
     H[P(2, 5)] = rt * e12;
-    H[P(3, 3)] = A22 + p.rva;
+    H[P(3, 3)] = A22 + rva;
     H[P(3, 4)] = -rt * e02;
     H[P(3, 5)] = -rt * e12;
     H[P(4, 4)] = rt;
@@ -190,63 +192,73 @@ __device__ __forceinline__ void hmul(const double *H, const double *v, double *o
     }
 }
 
+// q(s) = g's + s'Hs/2 using the symmetry of H
 __device__ __forceinline__ double qmodel(const double *g, const double *H, const double *s)
 {
-    double Hs[6];
-    hmul(H, s, Hs);
-    return dot6(g, s) + 0.5 * dot6(s, Hs);
+    double q = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double t = g[i] + 0.5 * H[P(i, i)] * s[i];
+#pragma unroll
+        for (int j = i + 1; j < 6; ++j) t += H[P(i, j)] * s[j];
+        q += s[i] * t;
+    }
+    return q;
 }
 
-__device__ __forceinline__ void pstep(const Prob &p, const double *x, const double *g,
-                                      double a, double *s)
+__device__ __forceinline__ void pstep(const Bounds &B, const double *x, const double *g, double a,
+                                      double *s)
 {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) s[i] = clampd(x[i] - a * g[i], p.lo[i], p.hi[i]) - x[i];
+    for (int i = 0; i < 6; ++i) s[i] = clampd(x[i] - a * g[i], B.lo(i), B.hi(i)) - x[i];
 }
 
-__device__ __forceinline__ double pgnorm(const Prob &p, const double *x, const double *g)
+__device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const double *g)
 {
     double m = 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) m = fmax(m, fabs(clampd(x[i] - g[i], p.lo[i], p.hi[i]) - x[i]));
+    for (int i = 0; i < 6; ++i) m = fmax(m, fabs(clampd(x[i] - g[i], B.lo(i), B.hi(i)) - x[i]));
     return m;
 }
 
 __device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, const double *s,
-                                          double delta)
+                                          double delta2)
 {
-    return sqrt(dot6(s, s)) <= delta && qmodel(g, H, s) <= kMu0 * dot6(g, s);
+    return dot6(s, s) <= delta2 && qmodel(g, H, s) <= kMu0 * dot6(g, s);
 }
 
 // generalised Cauchy step along the projected-gradient path
-__device__ void cauchy(const Prob &p, const double *x, const double *g, const double *H,
-                       double delta, double &alpha, double *s, Cnt &c)
+__device__ __forceinline__ void cauchy(const Bounds &B, const double *x, const double *g,
+                                       const double *H, double delta, double &alpha, double *s,
+                                       Cnt &c)
 {
     double brmax = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         double bp = 0.0;
-        if (g[i] > 0.0 && x[i] > p.lo[i]) bp = (x[i] - p.lo[i]) / g[i];
-        else if (g[i] < 0.0 && x[i] < p.hi[i]) bp = (x[i] - p.hi[i]) / g[i];
+        if (g[i] > 0.0 && x[i] > B.lo(i)) bp = (x[i] - B.lo(i)) / g[i];
+        else if (g[i] < 0.0 && x[i] < B.hi(i)) bp = (x[i] - B.hi(i)) / g[i];
         brmax = fmax(brmax, bp);
     }
+    const double d2 = delta * delta;
     double a = alpha;
-    pstep(p, x, g, a, s);
+    pstep(B, x, g, a, s);
     c.cauchy++;
-    if (!cauchy_ok(g, H, s, delta)) {
+    if (!cauchy_ok(g, H, s, d2)) {
         for (int t = 0; t < kCauchyTrials; ++t) {
             a *= 0.1;
-            pstep(p, x, g, a, s);
+            pstep(B, x, g, a, s);
             c.cauchy++;
-            if (cauchy_ok(g, H, s, delta)) break;
+            if (cauchy_ok(g, H, s, d2)) break;
         }
     } else {
         for (int t = 0; t < kCauchyTrials; ++t) {
             if (a >= brmax) break;
-            double an = a * 10.0, sn[6];
-            pstep(p, x, g, an, sn);
+            const double an = a * 10.0;
+            double sn[6];
+            pstep(B, x, g, an, sn);
             c.cauchy++;
-            if (!cauchy_ok(g, H, sn, delta)) break;
+            if (!cauchy_ok(g, H, sn, d2)) break;
             a = an;
 #pragma unroll
             for (int i = 0; i < 6; ++i) s[i] = sn[i];
@@ -257,41 +269,43 @@ __device__ void cauchy(const Prob &p, const double *x, const double *g, const do
 
 __device__ __forceinline__ double boundary_tau(const double *a, const double *pv, double delta)
 {
-    double pp = dot6(pv, pv), ap = dot6(a, pv), aa = dot6(a, a);
-    double rad = fmax(delta * delta - aa, 0.0);
-    double disc = sqrt(ap * ap + pp * rad);
+    const double pp = dot6(pv, pv), ap = dot6(a, pv), aa = dot6(a, a);
+    const double rad = fmax(delta * delta - aa, 0.0);
+    const double disc = sqrt(ap * ap + pp * rad);
     if (pp == 0.0) return 0.0;
     return ap > 0.0 ? rad / (ap + disc) : (disc - ap) / pp;
 }
 
-// Preconditioner: Cholesky of the scaled free block plus sigma I (identity on
-// fixed variables); L packed lower-triangular, d the diagonal scaling.
-__device__ void precond_factor(const double *H, const bool *fr, double *L, double *d)
+// Preconditioner: Cholesky factor of D^-1 A D^-1 + sigma I on the free block
+// (identity on fixed variables), D = diag(sqrt|A_ii|).  Keeps 1/D and, on the
+// diagonal of L, the reciprocal pivots, so the solves only multiply.
+__device__ __forceinline__ void precond_factor(const double *H, const bool *fr, double *L,
+                                               double *dinv)
 {
     bool pos = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double a = H[P(i, i)];
-        d[i] = (fr[i] && a != 0.0) ? sqrt(fabs(a)) : 1.0;
-        if (fr[i] && !(a > 0.0)) pos = false;
+        const double a = H[P(i, i)];
+        dinv[i] = (fr[i] && a != 0.0) ? rsqrt(fabs(a)) : 1.0;
+        pos = pos && (!fr[i] || a > 0.0);
     }
     double sigma = pos ? 0.0 : 1e-3;
     for (int tries = 0; tries < kCholTries; ++tries) {
         bool ok = true;
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            double dd = fr[j] ? H[P(j, j)] / (d[j] * d[j]) + sigma : 1.0;
+            double dd = fr[j] ? H[P(j, j)] * dinv[j] * dinv[j] + sigma : 1.0;
 #pragma unroll
             for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
             ok = ok && (dd > 0.0);
-            double ljj = sqrt(fmax(dd, 1e-300));
-            L[P(j, j)] = ljj;
+            const double linv = rsqrt(fmax(dd, 1e-300));
+            L[P(j, j)] = linv;
 #pragma unroll
             for (int i = j + 1; i < 6; ++i) {
-                double v = (fr[i] && fr[j]) ? H[P(i, j)] / (d[i] * d[j]) : 0.0;
+                double v = (fr[i] && fr[j]) ? H[P(i, j)] * dinv[i] * dinv[j] : 0.0;
 #pragma unroll
                 for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
-                L[P(i, j)] = v / ljj;
+                L[P(i, j)] = v * linv;
             }
         }
         if (ok) return;
@@ -304,32 +318,33 @@ __device__ void precond_factor(const double *H, const bool *fr, double *L, doubl
     }
 }
 
-__device__ __forceinline__ void precond_solve(const double *L, const double *d, const double *r,
+__device__ __forceinline__ void precond_solve(const double *L, const double *dinv, const double *r,
                                               double *z)
 {
     double t[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double v = r[i] / d[i];
+        double v = r[i] * dinv[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) v -= L[P(i, k)] * t[k];
-        t[i] = v / L[P(i, i)];
+        t[i] = v * L[P(i, i)];
     }
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
         double v = t[i];
 #pragma unroll
         for (int k = i + 1; k < 6; ++k) v -= L[P(k, i)] * t[k];
-        t[i] = v / L[P(i, i)];
+        t[i] = v * L[P(i, i)];
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) z[i] = t[i] / d[i];
+    for (int i = 0; i < 6; ++i) z[i] = t[i] * dinv[i];
 }
 
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
-__device__ void subspace(const Prob &p, const double *x, const double *g, const double *H,
-                         double delta, const double *sc, double *s, Cnt &c)
+__device__ __forceinline__ void subspace(const Bounds &B, const double *x, const double *g,
+                                         const double *H, double delta, const double *sc,
+                                         double *s, Cnt &c)
 {
     bool fr[6];
     double xc[6];
@@ -337,7 +352,7 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         xc[i] = x[i] + sc[i];
-        fr[i] = xc[i] > p.lo[i] && xc[i] < p.hi[i];
+        fr[i] = xc[i] > B.lo(i) && xc[i] < B.hi(i);
         any = any || fr[i];
         s[i] = sc[i];
     }
@@ -346,8 +361,8 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
     hmul(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
-    double L[21], d[6];
-    precond_factor(H, fr, L, d);
+    double L[21], dinv[6];
+    precond_factor(H, fr, L, dinv);
     double w[6], r[6], z[6], pv[6], q[6];
     double rn0 = 0.0;
 #pragma unroll
@@ -356,16 +371,16 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
         r[i] = fr[i] ? -gc[i] : 0.0;
         rn0 += r[i] * r[i];
     }
-    rn0 = sqrt(rn0);
     if (rn0 == 0.0) return;
-    precond_solve(L, d, r, z);
+    precond_solve(L, dinv, r, z);
     double rz = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         pv[i] = fr[i] ? z[i] : 0.0;
         rz += r[i] * pv[i];
     }
-    const double tol = kCgRtol * rn0;
+    const double tol2 = kCgRtol * kCgRtol * rn0;
+    const double d2 = delta * delta;
     for (int it = 0; it < kCgMaxit; ++it) {
         c.cg++;
         hmul(H, pv, q);
@@ -378,17 +393,15 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
         double cur[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) cur[i] = sc[i] + w[i];
-        if (kappa <= 0.0) {
-            double tau = boundary_tau(cur, pv, delta);
+        const double al = rz / kappa;
+        double nx2 = 0.0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) w[i] += tau * pv[i];
-            break;
+        for (int i = 0; i < 6; ++i) {
+            const double v = cur[i] + al * pv[i];
+            nx2 += v * v;
         }
-        double al = rz / kappa, nx[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) nx[i] = cur[i] + al * pv[i];
-        if (sqrt(dot6(nx, nx)) >= delta) {
-            double tau = boundary_tau(cur, pv, delta);
+        if (kappa <= 0.0 || nx2 >= d2) {   // negative curvature or trust-region boundary
+            const double tau = boundary_tau(cur, pv, delta);
 #pragma unroll
             for (int i = 0; i < 6; ++i) w[i] += tau * pv[i];
             break;
@@ -400,27 +413,27 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
             r[i] -= al * q[i];
             rn += r[i] * r[i];
         }
-        if (sqrt(rn) <= tol) break;
-        precond_solve(L, d, r, z);
+        if (rn <= tol2) break;
+        precond_solve(L, dinv, r, z);
         double rz1 = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             z[i] = fr[i] ? z[i] : 0.0;
             rz1 += r[i] * z[i];
         }
-        double be = rz1 / rz;
+        const double be = rz1 / rz;
         rz = rz1;
 #pragma unroll
         for (int i = 0; i < 6; ++i) pv[i] = z[i] + be * pv[i];
     }
-    double qc = qmodel(g, H, sc);
+    const double qc = qmodel(g, H, sc);
     double beta = 1.0;
     for (int t = 0; t < kPsTrials; ++t) {
         c.ps++;
         double sb[6], dd[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            sb[i] = clampd(xc[i] + beta * w[i], p.lo[i], p.hi[i]) - x[i];
+            sb[i] = clampd(xc[i] + beta * w[i], B.lo(i), B.hi(i)) - x[i];
             dd[i] = sb[i] - sc[i];
         }
         if (qmodel(g, H, sb) <= qc + kMu0 * dot6(gc, dd)) {
@@ -432,134 +445,177 @@ __device__ void subspace(const Prob &p, const double *x, const double *g, const 
     }
 }
 
-// TRON on eq. branch from x; returns 0 converged, 1 iteration cap, 2 stalled
-__device__ int tron(const Prob &p, double *x, const DevOpts &O, Cnt &c)
-{
-#pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = clampd(x[i], p.lo[i], p.hi[i]);
-    double g[6], H[21];
-    double f = fval(p, x);
-    fgh(p, x, g, H);
-    c.tron_calls++;
-    c.fgh++;
-    const double pg0 = pgnorm(p, x, g);
-    const double gtol = O.tron_gtol * fmax(pg0, 1.0);
-    double sp[6];
-    pstep(p, x, g, 1.0, sp);
-    double delta = sqrt(dot6(sp, sp));
-    double alpha = 1.0;
-    int status = 1;
-    for (int k = 0; k < O.tron_max_iter; ++k) {
-        if (pgnorm(p, x, g) <= gtol) { status = 0; break; }
-        c.tron_iters++;
-        double sc[6], s[6];
-        cauchy(p, x, g, H, delta, alpha, sc, c);
-        subspace(p, x, g, H, delta, sc, s, c);
-        double xn = 0.0, sn = 0.0;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            xn = fmax(xn, fabs(x[i]));
-            sn = fmax(sn, fabs(s[i]));
-        }
-        if (sn <= O.tron_xtol * fmax(xn, 1.0)) { status = 0; break; }
-        double xt[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) xt[i] = clampd(x[i] + s[i], p.lo[i], p.hi[i]);
-        double ft = fval(p, xt);
-        c.f++;
-        double prered = -qmodel(g, H, s);
-        double actred = f - ft;
-        double snorm = sqrt(dot6(s, s));
-        if (k == 0 && snorm < delta) delta = snorm;
-        double fa = fmax(fabs(f), 1.0);
-        double ratio;
-        if (prered <= 0.0) ratio = -1.0;
-        else if (prered <= O.tron_ftol * fa) ratio = 1.0;
-        else ratio = actred / prered;
-        if (ratio < kEta1) delta = kSigma1 * fmin(snorm, delta);
-        else if (ratio > kEta2) delta = fmax(delta, kSigma3 * snorm);
-        if (ratio > kEta0) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) x[i] = xt[i];
-            f = ft;
-            fgh(p, x, g, H);
-            c.fgh++;
-        }
-        if (prered <= 0.0) { status = 2; break; }
-        xn = 0.0;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) xn = fmax(xn, fabs(x[i]));
-        if (delta <= 1e-14 * fmax(xn, 1.0)) { status = 2; break; }
-    }
-    if (status == 1) c.maxhit++;
-    return status;
-}
-
 __device__ __forceinline__ void warp_add_u64(unsigned long long *dst, int v)
 {
-    unsigned int s = __reduce_add_sync(0xffffffffu, (unsigned int)v);
+    const unsigned int s = __reduce_add_sync(kFull, (unsigned int)v);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
+enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_DONE = 3 };
+
 }  // namespace
 
-__global__ void __launch_bounds__(kBranchBlock) branch_tron_kernel(DevGrid G, DevOpts O)
+__global__ void __launch_bounds__(kBranchBlock, kBranchBlocksPerSM)
+branch_tron_kernel(DevGrid G, DevOpts O)
 {
+    __shared__ double sh[16 * kBranchBlock];   // per lane: Y[8], t[8], stride kBranchBlock
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int nl = G.nl;
+    const int lane = threadIdx.x & 31;
+    const double *sY = sh + threadIdx.x;
+    const double *sT = sh + 8 * kBranchBlock + threadIdx.x;
+    const double rpq = ctrl->rho_pq, rva = ctrl->rho_va;
+    const double rt0 = O.al_rho0 > 0.0 ? O.al_rho0 : rpq;
     Cnt c = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (l < nl) {
-        Prob p;
+
+    int b = -1, state = LS_IDLE, apass = 0, k = 0;
+    bool exhausted = false;
+    Bounds B{1.0, 1.0, 1.0, 1.0, 0.0};
+    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, g[6], H[21], F[4] = {0.0, 0.0, 0.0, 0.0};
+    double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0;
+    double lt0 = 0.0, lt1 = 0.0, rt = rt0, hprev = 0.0;
+
+    while (true) {
+        // (A) a finished TRON solve: line-limit multiplier update (Section II-C)
+        if (state == LS_DONE) {
+            const double h0 = F[0] * F[0] + F[1] * F[1] + x[4];
+            const double h1 = F[2] * F[2] + F[3] * F[3] + x[5];
+            lt0 += rt * h0;
+            lt1 += rt * h1;
+            const double hm = fmax(fabs(h0), fabs(h1));
+            bool fin = hm <= O.al_tol;
+            if (!fin) {
+                if (hm > O.al_decay * hprev) rt = fmin(rt * O.al_rho_factor, O.al_rho_max);
+                hprev = hm;
+                fin = apass >= O.al_max_iter;
+            }
+            if (fin) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            p.Y[k] = G.Y[k * nl + l];
-            p.t[k] = G.bt[k * nl + l];
+                for (int i = 0; i < 6; ++i) G.bx[i * nl + b] = x[i];
+                G.blt[b] = lt0;
+                G.blt[nl + b] = lt1;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) G.bu[i * nl + b] = F[i];
+                G.bu[4 * nl + b] = x[0] * x[0];
+                G.bu[5 * nl + b] = x[2];
+                G.bu[6 * nl + b] = x[1] * x[1];
+                G.bu[7 * nl + b] = x[3];
+                b = -1;
+                state = LS_IDLE;
+            } else {
+                state = LS_INIT;
+            }
         }
-        p.lo[0] = G.lim[0 * nl + l]; p.hi[0] = G.lim[1 * nl + l];
-        p.lo[1] = G.lim[2 * nl + l]; p.hi[1] = G.lim[3 * nl + l];
-        p.lo[2] = -kTwoPi; p.hi[2] = kTwoPi;
-        p.lo[3] = -kTwoPi; p.hi[3] = kTwoPi;
-        p.lo[4] = G.lim[4 * nl + l]; p.hi[4] = 0.0;
-        p.lo[5] = p.lo[4]; p.hi[5] = 0.0;
-        p.rpq = ctrl->rho_pq;
-        p.rva = ctrl->rho_va;
-        p.lt0 = G.blt[l];
-        p.lt1 = G.blt[nl + l];
-        p.rt = O.al_rho0 > 0.0 ? O.al_rho0 : p.rpq;
-        double x[6];
+        // (R) refill idle lanes from the branch queue (one atomic per warp)
+        const unsigned need = __ballot_sync(kFull, state == LS_IDLE && !exhausted);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&ctrl->branch_next, (unsigned)__popc(need));
+            base = __shfl_sync(kFull, base, leader);
+            if (state == LS_IDLE && !exhausted) {
+                const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
+                if (idx < (unsigned)nl) {
+                    b = (int)idx;
+                    double *my = sh + threadIdx.x;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) x[k] = G.bx[k * nl + l];
-        // augmented Lagrangian on p^2 + q^2 + s = 0 of both ends
-        double hprev = __longlong_as_double(0x7ff0000000000000LL);
-        Flow fl[4];
-        for (int a = 0; a < O.al_max_iter; ++a) {
+                    for (int i = 0; i < 8; ++i) {
+                        my[i * kBranchBlock] = G.Y[i * nl + b];
+                        my[(8 + i) * kBranchBlock] = G.bt[i * nl + b];
+                    }
+                    B.vlo_i = G.lim[0 * nl + b];
+                    B.vhi_i = G.lim[1 * nl + b];
+                    B.vlo_j = G.lim[2 * nl + b];
+                    B.vhi_j = G.lim[3 * nl + b];
+                    B.slo = G.lim[4 * nl + b];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
+                    lt0 = G.blt[b];
+                    lt1 = G.blt[nl + b];
+                    rt = rt0;
+                    hprev = __longlong_as_double(0x7ff0000000000000LL);
+                    apass = 0;
+                    state = LS_INIT;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, state != LS_IDLE)) break;
+        // (I) start a TRON solve from the branch's current point
+        if (state == LS_INIT) {
+            apass++;
             c.al++;
-            tron(p, x, O, c);
-            flows4(p, x, fl, false);
-            double h0 = fl[0].F * fl[0].F + fl[1].F * fl[1].F + x[4];
-            double h1 = fl[2].F * fl[2].F + fl[3].F * fl[3].F + x[5];
-            p.lt0 += p.rt * h0;
-            p.lt1 += p.rt * h1;
-            double hm = fmax(fabs(h0), fabs(h1));
-            if (hm <= O.al_tol) break;
-            if (hm > O.al_decay * hprev) p.rt = fmin(p.rt * O.al_rho_factor, O.al_rho_max);
-            hprev = hm;
-        }
-        if (O.al_max_iter <= 0) flows4(p, x, fl, false);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) G.bx[k * nl + l] = x[k];
-        G.blt[l] = p.lt0;
-        G.blt[nl + l] = p.lt1;
-        G.bu[0 * nl + l] = fl[0].F;
-        G.bu[1 * nl + l] = fl[1].F;
-        G.bu[2 * nl + l] = fl[2].F;
-        G.bu[3 * nl + l] = fl[3].F;
-        G.bu[4 * nl + l] = x[0] * x[0];
-        G.bu[5 * nl + l] = x[2];
-        G.bu[6 * nl + l] = x[1] * x[1];
-        G.bu[7 * nl + l] = x[3];
+            for (int i = 0; i < 6; ++i) x[i] = clampd(x[i], B.lo(i), B.hi(i));
+            evaluate(sY, sT, rpq, rva, lt0, lt1, rt, x, f, g, H, F);
+            c.tron_calls++;
+            c.fgh++;
+            gtol = O.tron_gtol * fmax(pgnorm(B, x, g), 1.0);
+            double sp[6];
+            pstep(B, x, g, 1.0, sp);
+            delta = sqrt(dot6(sp, sp));
+            alpha = 1.0;
+            k = 0;
+            state = LS_ITER;
+        }
+        // (T) one TRON iteration
+        if (state == LS_ITER) {
+            if (k >= O.tron_max_iter) {
+                c.maxhit++;
+                state = LS_DONE;
+            } else if (pgnorm(B, x, g) <= gtol) {
+                state = LS_DONE;
+            } else {
+                c.tron_iters++;
+                double sc[6], s[6];
+                cauchy(B, x, g, H, delta, alpha, sc, c);
+                subspace(B, x, g, H, delta, sc, s, c);
+                double xn = 0.0, sn = 0.0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    xn = fmax(xn, fabs(x[i]));
+                    sn = fmax(sn, fabs(s[i]));
+                }
+                if (sn <= O.tron_xtol * fmax(xn, 1.0)) {
+                    state = LS_DONE;
+                } else {
+                    const double prered = -qmodel(g, H, s);
+                    c.f++;
+                    if (prered <= 0.0) {
+                        state = LS_DONE;          // no decrease predicted: stalled
+                    } else {
+                        double xt[6];
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) xt[i] = clampd(x[i] + s[i], B.lo(i), B.hi(i));
+                        const double snorm = sqrt(dot6(s, s));
+                        double ft;
+                        evaluate(sY, sT, rpq, rva, lt0, lt1, rt, xt, ft, g, H, F);
+                        const double actred = f - ft;
+                        if (k == 0 && snorm < delta) delta = snorm;
+                        const double fa = fmax(fabs(f), 1.0);
+                        const double ratio = prered <= O.tron_ftol * fa ? 1.0 : actred / prered;
+                        if (ratio < kEta1) delta = kSigma1 * fmin(snorm, delta);
+                        else if (ratio > kEta2) delta = fmax(delta, kSigma3 * snorm);
+                        if (ratio > kEta0) {
+#pragma unroll
+                            for (int i = 0; i < 6; ++i) x[i] = xt[i];
+                            f = ft;
+                            c.fgh++;
+                        } else {
+                            double fk;
+                            evaluate(sY, sT, rpq, rva, lt0, lt1, rt, x, fk, g, H, F);
+                        }
+                        xn = 0.0;
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) xn = fmax(xn, fabs(x[i]));
+                        if (delta <= 1e-14 * fmax(xn, 1.0)) state = LS_DONE;
+                        ++k;
+                    }
+                }
+            }
+        }
     }
     unsigned long long *st = ctrl->stats;
     warp_add_u64(&st[ST_TRON_CALLS], c.tron_calls);

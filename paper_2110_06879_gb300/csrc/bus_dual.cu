@@ -189,6 +189,7 @@ __global__ void begin_kernel(DevGrid G, DevOpts O, SolveParams P)
     c->zprev = __longlong_as_double(0x7ff0000000000000LL);
     c->tol_in = fmax(O.tol_in0, P.tol);
     c->counter = 0;
+    c->branch_next = 0;
     for (int k = 0; k < kNumStats; ++k) c->stats[k] = 0;
 }
 
@@ -343,6 +344,7 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     if (threadIdx.x != 0) return;
     Ctrl *c = ctrl;
     c->counter = 0;
+    c->branch_next = 0;     // the next branch_tron launch starts its queue at 0
     const double pri = sqrt(v[0]), pri_z = sqrt(v[1]), dual = sqrt(v[2]), zn = sqrt(v[3]);
     c->pri = pri; c->pri_z = pri_z; c->dual = dual; c->zn = zn;
     double *h = G.hist + 4 * (c->iter % kHistCap);

@@ -293,7 +293,16 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
         std::vector<int32_t> fill(h->row_ptr.begin(), h->row_ptr.end() - 1);
         for (int e = 0; e < ns; ++e) h->col[fill[bus_of(e)]++] = e;
     }
-    h->nblk_branch = (nl + kBranchBlock - 1) / kBranchBlock;
+    {
+        // branch_tron is persistent: at most kBranchBlocksPerSM blocks per SM
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 152;
+        cudaGetLastError();
+        const int need = (nl + kBranchBlock - 1) / kBranchBlock;
+        h->nblk_branch = need < sms * kBranchBlocksPerSM ? need : sms * kBranchBlocksPerSM;
+    }
     h->nblk_bus = (nb + kBusBlock - 1) / kBusBlock;
     h->nblk_cold = (nl + ns + nb + ng + 1 + 255) / 256;
     h->nblk_fin = (nb + nl + ng + kFinBlock - 1) / kFinBlock;
@@ -334,6 +343,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     DevGrid &G = h->G;
     G.nb = nb; G.nl = nl; G.ng = ng; G.ns = ns; G.ref = h->ref;
     G.nblk_bus = h->nblk_bus;
+    G.nblk_branch = h->nblk_branch;
     G.f_bus = (int32_t *)(base + o_fb); G.t_bus = (int32_t *)(base + o_tb);
     G.Y = (double *)(base + o_Y); G.lim = (double *)(base + o_lim);
     G.bx = (double *)(base + o_bx); G.blt = (double *)(base + o_blt);
