@@ -96,6 +96,7 @@ typedef struct {
     int32_t al_max_iter;   /* 20 */
     int32_t tron_max_iter; /* 200 */
     int32_t use_graph;     /* 1: conditional-WHILE CUDA graph; 0: stream launches   */
+    int32_t branch_blocks; /* resident blocks of 128 branch lanes; 0: 2 per SM          */
 } admm_options;
 
 typedef struct {

@@ -44,6 +44,9 @@ struct Ctrl {
     unsigned int fin_counter;      // last-block detection of finalize
     unsigned int branch_next;      // work queue head of branch_tron (reset every iteration)
     unsigned int pad1;
+    // longest-first scheduling of branch_tron: branches filed by the loop trips
+    // they needed, three classes, double-buffered by iteration parity
+    unsigned int cls_count[2][4];
     unsigned long long stats[kNumStats];
 };
 
@@ -73,6 +76,7 @@ struct DevGrid {
     // slots
     double *sx, *sz, *sy, *sl;
     // scratch and control
+    int32_t *cls_list;             // [2][3][nl] branch ids per (parity, class)
     double *partials;              // [nblk_bus][4]
     double *fin_partials;          // [nblk_fin][2]
     double *hist;                  // [kHistCap][4]
@@ -97,7 +101,7 @@ __global__ void finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, d
                                 double *pf, double *qf, double *pt, double *qt, int32_t nblk);
 
 constexpr int kBranchBlock = 128;
-constexpr int kBranchBlocksPerSM = 2;
+constexpr int kBranchBlocksPerSM = 1;
 constexpr int kBusBlock = 256;
 constexpr int kFinBlock = 256;
 

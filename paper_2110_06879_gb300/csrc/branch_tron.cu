@@ -227,42 +227,44 @@ __device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, cons
     return dot6(s, s) <= delta2 && qmodel(g, H, s) <= kMu0 * dot6(g, s);
 }
 
-// generalised Cauchy step along the projected-gradient path
+// Generalised Cauchy step along the projected-gradient path: from the carried
+// alpha, backtrack by 0.1 while the sufficient-decrease / radius test fails, or
+// extrapolate by 10 while it holds and the path still moves.  Both directions
+// share one loop body so a warp runs them together.
 __device__ __forceinline__ void cauchy(const Bounds &B, const double *x, const double *g,
                                        const double *H, double delta, double &alpha, double *s,
                                        Cnt &c)
 {
-    double brmax = 0.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double bp = 0.0;
-        if (g[i] > 0.0 && x[i] > B.lo(i)) bp = (x[i] - B.lo(i)) / g[i];
-        else if (g[i] < 0.0 && x[i] < B.hi(i)) bp = (x[i] - B.hi(i)) / g[i];
-        brmax = fmax(brmax, bp);
-    }
     const double d2 = delta * delta;
     double a = alpha;
     pstep(B, x, g, a, s);
     c.cauchy++;
-    if (!cauchy_ok(g, H, s, d2)) {
-        for (int t = 0; t < kCauchyTrials; ++t) {
-            a *= 0.1;
-            pstep(B, x, g, a, s);
-            c.cauchy++;
-            if (cauchy_ok(g, H, s, d2)) break;
+    const bool back = !cauchy_ok(g, H, s, d2);
+    bool go = true;
+    for (int t = 0; t < kCauchyTrials; ++t) {
+        if (!back) {
+            // stop once a is at or past every breakpoint of the projected path,
+            // i.e. a g_i >= x_i - l_i (g_i > 0) and a g_i <= x_i - u_i (g_i < 0)
+            bool past = true;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                if (g[i] > 0.0 && x[i] > B.lo(i)) past = past && a * g[i] >= x[i] - B.lo(i);
+                else if (g[i] < 0.0 && x[i] < B.hi(i)) past = past && a * g[i] <= x[i] - B.hi(i);
+            }
+            if (past) go = false;
         }
-    } else {
-        for (int t = 0; t < kCauchyTrials; ++t) {
-            if (a >= brmax) break;
-            const double an = a * 10.0;
-            double sn[6];
-            pstep(B, x, g, an, sn);
-            c.cauchy++;
-            if (!cauchy_ok(g, H, sn, d2)) break;
+        if (!go) break;
+        const double an = back ? a * 0.1 : a * 10.0;
+        double sn[6];
+        pstep(B, x, g, an, sn);
+        c.cauchy++;
+        const bool ok = cauchy_ok(g, H, sn, d2);
+        if (back || ok) {
             a = an;
 #pragma unroll
             for (int i = 0; i < 6; ++i) s[i] = sn[i];
         }
+        if (ok == back) go = false;    // backtracking found a point / extrapolation failed
     }
     alpha = a;
 }
@@ -279,9 +281,37 @@ __device__ __forceinline__ double boundary_tau(const double *a, const double *pv
 // Preconditioner: Cholesky factor of D^-1 A D^-1 + sigma I on the free block
 // (identity on fixed variables), D = diag(sqrt|A_ii|).  Keeps 1/D and, on the
 // diagonal of L, the reciprocal pivots, so the solves only multiply.
+__device__ __forceinline__ bool chol_plain(const double *H, const bool *fr, double *L)
+{
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double dd = fr[j] ? H[P(j, j)] : 1.0;
+#pragma unroll
+        for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
+        ok = ok && (dd > 0.0);
+        const double linv = rsqrt(fmax(dd, 1e-300));
+        L[P(j, j)] = linv;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            double v = (fr[i] && fr[j]) ? H[P(i, j)] : 0.0;
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
+            L[P(i, j)] = v * linv;
+        }
+    }
+    return ok;
+}
+
 __device__ __forceinline__ void precond_factor(const double *H, const bool *fr, double *L,
                                                double *dinv)
 {
+    // A positive definite free block is factored as is: D L L' D with D the
+    // diagonal scaling equals L L' exactly then, so the preconditioned CG
+    // iterates are the same.  Otherwise scale and shift.
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dinv[i] = 1.0;
+    if (chol_plain(H, fr, L)) return;
     bool pos = true;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -451,7 +481,7 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long *dst, int v)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
-enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_DONE = 3 };
+enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE = 4 };
 
 }  // namespace
 
@@ -469,15 +499,60 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     const double rt0 = O.al_rho0 > 0.0 ? O.al_rho0 : rpq;
     Cnt c = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
-    int b = -1, state = LS_IDLE, apass = 0, k = 0;
+    // queue order: the classes filed by the previous iteration, hardest first
+    const int cur = ctrl->total_iters & 1, nxt = cur ^ 1;
+    const unsigned n0 = ctrl->cls_count[cur][0], n1 = ctrl->cls_count[cur][1];
+    const unsigned n2 = ctrl->cls_count[cur][2];
+    const bool ordered = n0 + n1 + n2 == (unsigned)nl;
+    const int32_t *lcur = G.cls_list + (size_t)cur * 3 * nl;
+    int32_t *lnxt = G.cls_list + (size_t)nxt * 3 * nl;
+
+    int b = -1, state = LS_IDLE, apass = 0, k = 0, trips = 0;
     bool exhausted = false;
     Bounds B{1.0, 1.0, 1.0, 1.0, 0.0};
-    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, g[6], H[21], F[4] = {0.0, 0.0, 0.0, 0.0};
-    double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0;
+    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xt[6], g[6], H[21], F[4] = {0.0, 0.0, 0.0, 0.0};
+    double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0, prered = 0.0, snorm = 0.0;
     double lt0 = 0.0, lt1 = 0.0, rt = rt0, hprev = 0.0;
 
     while (true) {
-        // (A) a finished TRON solve: line-limit multiplier update (Section II-C)
+        bool eval = false;
+        // (T) one TRON iteration up to its trial point, or the stop of the solve
+        if (state == LS_ITER) {
+            if (k >= O.tron_max_iter) {
+                c.maxhit++;
+                state = LS_DONE;
+            } else if (pgnorm(B, x, g) <= gtol) {
+                state = LS_DONE;
+            } else {
+                c.tron_iters++;
+                double sc[6], s[6];
+                cauchy(B, x, g, H, delta, alpha, sc, c);
+                subspace(B, x, g, H, delta, sc, s, c);
+                double xn = 0.0, sn = 0.0;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    xn = fmax(xn, fabs(x[i]));
+                    sn = fmax(sn, fabs(s[i]));
+                }
+                if (sn <= O.tron_xtol * fmax(xn, 1.0)) {
+                    state = LS_DONE;
+                } else {
+                    prered = -qmodel(g, H, s);
+                    c.f++;
+                    if (prered <= 0.0) {
+                        state = LS_DONE;          // no decrease predicted: stalled
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) xt[i] = clampd(x[i] + s[i], B.lo(i), B.hi(i));
+                        snorm = sqrt(dot6(s, s));
+                        eval = true;
+                    }
+                }
+            }
+        }
+        // (A) a finished TRON solve: line-limit multiplier update (Section II-C);
+        // the next pass starts in this same trip
+        int filed = -1, fcls = 0;
         if (state == LS_DONE) {
             const double h0 = F[0] * F[0] + F[1] * F[1] + x[4];
             const double h1 = F[2] * F[2] + F[3] * F[3] + x[5];
@@ -501,10 +576,25 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 G.bu[5 * nl + b] = x[2];
                 G.bu[6 * nl + b] = x[1] * x[1];
                 G.bu[7 * nl + b] = x[3];
+                filed = b;
+                fcls = trips >= 24 ? 0 : trips >= 8 ? 1 : 2;
                 b = -1;
                 state = LS_IDLE;
             } else {
                 state = LS_INIT;
+            }
+        }
+        // (F) file finished branches by the work they took (one atomic per class and warp)
+#pragma unroll
+        for (int cl = 0; cl < 3; ++cl) {
+            const unsigned m = __ballot_sync(kFull, filed >= 0 && fcls == cl);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(&ctrl->cls_count[nxt][cl], (unsigned)__popc(m));
+                base = __shfl_sync(kFull, base, leader);
+                if (filed >= 0 && fcls == cl)
+                    lnxt[(size_t)cl * nl + base + __popc(m & ((1u << lane) - 1u))] = filed;
             }
         }
         // (R) refill idle lanes from the branch queue (one atomic per warp)
@@ -517,7 +607,11 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             if (state == LS_IDLE && !exhausted) {
                 const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
                 if (idx < (unsigned)nl) {
-                    b = (int)idx;
+                    b = !ordered ? (int)idx
+                        : idx < n0 ? lcur[idx]
+                        : idx < n0 + n1 ? lcur[nl + (idx - n0)]
+                                        : lcur[2 * (size_t)nl + (idx - n0 - n1)];
+                    trips = 0;
                     double *my = sh + threadIdx.x;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -543,13 +637,29 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             }
         }
         if (!__any_sync(kFull, state != LS_IDLE)) break;
-        // (I) start a TRON solve from the branch's current point
+        // (I) a TRON solve starts from the current point; a rejected step gets
+        // its gradient and Hessian back at the kept point
         if (state == LS_INIT) {
             apass++;
             c.al++;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) x[i] = clampd(x[i], B.lo(i), B.hi(i));
-            evaluate(sY, sT, rpq, rva, lt0, lt1, rt, x, f, g, H, F);
+            for (int i = 0; i < 6; ++i) {
+                x[i] = clampd(x[i], B.lo(i), B.hi(i));
+                xt[i] = x[i];
+            }
+            eval = true;
+        } else if (state == LS_REEVAL) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xt[i] = x[i];
+            eval = true;
+        }
+        // (E) the one evaluation site of the trip
+        double fe = 0.0;
+        if (eval) evaluate(sY, sT, rpq, rva, lt0, lt1, rt, xt, fe, g, H, F);
+        if (b >= 0) ++trips;
+        // (Q) after the evaluation
+        if (state == LS_INIT) {
+            f = fe;
             c.tron_calls++;
             c.fgh++;
             gtol = O.tron_gtol * fmax(pgnorm(B, x, g), 1.0);
@@ -559,62 +669,28 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             alpha = 1.0;
             k = 0;
             state = LS_ITER;
-        }
-        // (T) one TRON iteration
-        if (state == LS_ITER) {
-            if (k >= O.tron_max_iter) {
-                c.maxhit++;
-                state = LS_DONE;
-            } else if (pgnorm(B, x, g) <= gtol) {
-                state = LS_DONE;
+        } else if (state == LS_REEVAL) {
+            state = LS_ITER;
+        } else if (state == LS_ITER && eval) {
+            const double actred = f - fe;
+            if (k == 0 && snorm < delta) delta = snorm;
+            const double fa = fmax(fabs(f), 1.0);
+            const double ratio = prered <= O.tron_ftol * fa ? 1.0 : actred / prered;
+            if (ratio < kEta1) delta = kSigma1 * fmin(snorm, delta);
+            else if (ratio > kEta2) delta = fmax(delta, kSigma3 * snorm);
+            if (ratio > kEta0) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) x[i] = xt[i];
+                f = fe;
+                c.fgh++;
             } else {
-                c.tron_iters++;
-                double sc[6], s[6];
-                cauchy(B, x, g, H, delta, alpha, sc, c);
-                subspace(B, x, g, H, delta, sc, s, c);
-                double xn = 0.0, sn = 0.0;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    xn = fmax(xn, fabs(x[i]));
-                    sn = fmax(sn, fabs(s[i]));
-                }
-                if (sn <= O.tron_xtol * fmax(xn, 1.0)) {
-                    state = LS_DONE;
-                } else {
-                    const double prered = -qmodel(g, H, s);
-                    c.f++;
-                    if (prered <= 0.0) {
-                        state = LS_DONE;          // no decrease predicted: stalled
-                    } else {
-                        double xt[6];
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) xt[i] = clampd(x[i] + s[i], B.lo(i), B.hi(i));
-                        const double snorm = sqrt(dot6(s, s));
-                        double ft;
-                        evaluate(sY, sT, rpq, rva, lt0, lt1, rt, xt, ft, g, H, F);
-                        const double actred = f - ft;
-                        if (k == 0 && snorm < delta) delta = snorm;
-                        const double fa = fmax(fabs(f), 1.0);
-                        const double ratio = prered <= O.tron_ftol * fa ? 1.0 : actred / prered;
-                        if (ratio < kEta1) delta = kSigma1 * fmin(snorm, delta);
-                        else if (ratio > kEta2) delta = fmax(delta, kSigma3 * snorm);
-                        if (ratio > kEta0) {
-#pragma unroll
-                            for (int i = 0; i < 6; ++i) x[i] = xt[i];
-                            f = ft;
-                            c.fgh++;
-                        } else {
-                            double fk;
-                            evaluate(sY, sT, rpq, rva, lt0, lt1, rt, x, fk, g, H, F);
-                        }
-                        xn = 0.0;
-#pragma unroll
-                        for (int i = 0; i < 6; ++i) xn = fmax(xn, fabs(x[i]));
-                        if (delta <= 1e-14 * fmax(xn, 1.0)) state = LS_DONE;
-                        ++k;
-                    }
-                }
+                state = LS_REEVAL;
             }
+            double xn = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) xn = fmax(xn, fabs(x[i]));
+            if (delta <= 1e-14 * fmax(xn, 1.0)) state = LS_DONE;
+            ++k;
         }
     }
     unsigned long long *st = ctrl->stats;

@@ -167,6 +167,8 @@ __global__ void cold_start_kernel(DevGrid G, double beta_init)
         c->beta = beta_init;
         c->pending = 0;
         c->total_iters = 0;
+        for (int q = 0; q < 2; ++q)
+            for (int r = 0; r < 4; ++r) c->cls_count[q][r] = 0u;
     }
 }
 
@@ -351,6 +353,12 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     h[0] = pri; h[1] = dual; h[2] = zn; h[3] = pri_z;
     c->iter += 1;
     c->total_iters += 1;
+    // the branch lists filled by this iteration become the next queue order;
+    // the ones it consumed are emptied to be filled next
+    {
+        const int nxt = (c->total_iters + 1) & 1;
+        for (int r = 0; r < 4; ++r) c->cls_count[nxt][r] = 0u;
+    }
     int stop = 0;
     c->pending = 0;
     if (!isfinite(pri) || !isfinite(dual) || !isfinite(zn)) {

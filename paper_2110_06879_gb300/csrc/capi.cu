@@ -96,6 +96,7 @@ extern "C" void admm_default_options(admm_options *o)
     o->al_max_iter = 20;
     o->tron_max_iter = 200;
     o->use_graph = 1;
+    o->branch_blocks = 0;
 }
 
 extern "C" const char *admm_last_error(void) { return g_err.c_str(); }
@@ -165,6 +166,7 @@ int validate(const admm_grid *g, const admm_options *o)
     }
     if (o) {
         if (!(o->rho_pq > 0.0) || !(o->rho_va > 0.0)) { set_err("penalties must be positive"); return ADMM_ERR_INVALID_ARG; }
+        if (o->branch_blocks < 0) { set_err("branch_blocks must be >= 0"); return ADMM_ERR_INVALID_ARG; }
         if (o->max_outer < 1 || o->max_inner < 1 || o->tron_max_iter < 1 || o->al_max_iter < 1) {
             set_err("iteration caps must be >= 1");
             return ADMM_ERR_INVALID_ARG;
@@ -301,7 +303,8 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
             sms = 152;
         cudaGetLastError();
         const int need = (nl + kBranchBlock - 1) / kBranchBlock;
-        h->nblk_branch = need < sms * kBranchBlocksPerSM ? need : sms * kBranchBlocksPerSM;
+        const int cap = h->opts.branch_blocks > 0 ? h->opts.branch_blocks : sms * kBranchBlocksPerSM;
+        h->nblk_branch = need < cap ? need : cap;
     }
     h->nblk_bus = (nb + kBusBlock - 1) / kBusBlock;
     h->nblk_cold = (nl + ns + nb + ng + 1 + 255) / 256;
@@ -321,6 +324,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     size_t o_rp = cv.take<int32_t>(nb + 1), o_col = cv.take<int32_t>(ns);
     size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
     size_t o_sy = cv.take<double>(4 * (size_t)ns), o_sl = cv.take<double>(4 * (size_t)ns);
+    size_t o_cls = cv.take<int32_t>(6 * (size_t)nl);
     size_t o_part = cv.take<double>(4 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
     size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
     size_t o_ctrl = cv.take<Ctrl>(1);
@@ -355,6 +359,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     G.row_ptr = (int32_t *)(base + o_rp); G.col = (int32_t *)(base + o_col);
     G.sx = (double *)(base + o_sx); G.sz = (double *)(base + o_sz);
     G.sy = (double *)(base + o_sy); G.sl = (double *)(base + o_sl);
+    G.cls_list = (int32_t *)(base + o_cls);
     G.partials = (double *)(base + o_part); G.fin_partials = (double *)(base + o_fpart);
     G.hist = (double *)(base + o_hist);
     G.ctrl = (Ctrl *)(base + o_ctrl);
@@ -771,6 +776,7 @@ extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
     h->hctrl->beta_used = sc[2];
     h->hctrl->pending = (int32_t)sc[3];
     h->hctrl->done = 0;
+    std::memset(h->hctrl->cls_count, 0, sizeof(h->hctrl->cls_count));   // queue order restarts
     const double *p = sc + 4;
     for (auto &pt : parts) {
         if (pt.n) CK(cudaMemcpyAsync(pt.dev, p, pt.n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
