@@ -43,9 +43,43 @@ struct Cnt {
     int tron_calls, tron_iters, fgh, f, cauchy, cg, ps, al, maxhit;
 };
 
-// bounds of one branch: v_i, v_j from the buses, theta copies +-2 pi, slacks
+// Order-preserving integer images of doubles (NaN excluded, -0 == +0).
+// GB300 executes double compare / min / max on the FP64 pipe at the FP64 rate,
+// so every comparison, min, max and clamp of the solver runs on these keys on
+// the integer pipe instead; only arithmetic uses the FP64 pipe.
+__device__ __forceinline__ long long okey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    const long long m = b & 0x7fffffffffffffffLL;
+    return b < 0 ? -m : m;
+}
+__device__ __forceinline__ bool dlt(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ bool dle(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ bool dpos(double a) { return __double_as_longlong(a) > 0; }   // a > 0
+__device__ __forceinline__ bool dneg(double a) { return okey(a) < 0; }                   // a < 0
+__device__ __forceinline__ double dmaxi(double a, double b) { return dlt(a, b) ? b : a; }
+__device__ __forceinline__ double dmini(double a, double b) { return dlt(b, a) ? b : a; }
+__device__ __forceinline__ double dabsi(double a)
+{
+    return __longlong_as_double(__double_as_longlong(a) & 0x7fffffffffffffffLL);
+}
+// max of |a| over values: the bits of non-negative doubles order like integers
+__device__ __forceinline__ double amax(double m, double a)
+{
+    const long long ba = __double_as_longlong(a) & 0x7fffffffffffffffLL;
+    return ba > __double_as_longlong(m) ? __longlong_as_double(ba) : m;
+}
+
+// bounds of one branch: v_i, v_j from the buses, theta copies +-2 pi, slacks;
+// kept with their keys
 struct Bounds {
     double vlo_i, vhi_i, vlo_j, vhi_j, slo;
+    long long kvlo_i, kvhi_i, kvlo_j, kvhi_j, kslo;
+    __device__ __forceinline__ void set_keys()
+    {
+        kvlo_i = okey(vlo_i); kvhi_i = okey(vhi_i); kvlo_j = okey(vlo_j); kvhi_j = okey(vhi_j);
+        kslo = okey(slo);
+    }
     __device__ __forceinline__ double lo(int i) const
     {
         return i == 0 ? vlo_i : i == 1 ? vlo_j : i < 4 ? -kTwoPi : slo;
@@ -54,12 +88,23 @@ struct Bounds {
     {
         return i == 0 ? vhi_i : i == 1 ? vhi_j : i < 4 ? kTwoPi : 0.0;
     }
+    __device__ __forceinline__ long long klo(int i) const
+    {
+        return i == 0 ? kvlo_i : i == 1 ? kvlo_j : i < 4 ? -0x401921FB54442D18LL : kslo;
+    }
+    __device__ __forceinline__ long long khi(int i) const
+    {
+        return i == 0 ? kvhi_i : i == 1 ? kvhi_j : i < 4 ? 0x401921FB54442D18LL : 0LL;
+    }
+    // P_[lo_i, hi_i](v)
+    __device__ __forceinline__ double clamp(int i, double v) const
+    {
+        const long long k = okey(v);
+        return k < klo(i) ? lo(i) : (k > khi(i) ? hi(i) : v);
+    }
+    __device__ __forceinline__ bool above_lo(int i, double v) const { return okey(v) > klo(i); }
+    __device__ __forceinline__ bool below_hi(int i, double v) const { return okey(v) < khi(i); }
 };
-
-__device__ __forceinline__ double clampd(double v, double lo, double hi)
-{
-    return fmin(fmax(v, lo), hi);
-}
 
 // One flow a_self v_k^2 + v_i v_j (alpha cos th + beta sin th): value, gradient
 // in (v_i, v_j, th) and Hessian entries (ii, jj, ij, i-th, j-th, th-th).
@@ -210,141 +255,163 @@ __device__ __forceinline__ void pstep(const Bounds &B, const double *x, const do
                                       double *s)
 {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) s[i] = clampd(x[i] - a * g[i], B.lo(i), B.hi(i)) - x[i];
+    for (int i = 0; i < 6; ++i) s[i] = B.clamp(i, x[i] - a * g[i]) - x[i];
 }
 
 __device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const double *g)
 {
     double m = 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) m = fmax(m, fabs(clampd(x[i] - g[i], B.lo(i), B.hi(i)) - x[i]));
+    for (int i = 0; i < 6; ++i) m = amax(m, B.clamp(i, x[i] - g[i]) - x[i]);
     return m;
 }
 
 __device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, const double *s,
                                           double delta2)
 {
-    return dot6(s, s) <= delta2 && qmodel(g, H, s) <= kMu0 * dot6(g, s);
+    return dle(dot6(s, s), delta2) && dle(qmodel(g, H, s), kMu0 * dot6(g, s));
 }
+
+// The loops below (Cauchy trials, Cholesky retries, CG, projected search)
+// have data-dependent trip counts.  They are written warp-uniform: every lane
+// of the warp runs every trip, exits are decided with __any_sync, and lanes
+// that are finished (or have no TRON iteration this trip, flag `on`) keep
+// their values by selection.  Lanes at different trips would otherwise be
+// scheduled apart and the warp would run their FP64 work one group after
+// another.  Inactive lanes compute on stale registers only (no memory access).
 
 // Generalised Cauchy step along the projected-gradient path: from the carried
 // alpha, backtrack by 0.1 while the sufficient-decrease / radius test fails, or
-// extrapolate by 10 while it holds and the path still moves.  Both directions
-// share one loop body so a warp runs them together.
-__device__ __forceinline__ void cauchy(const Bounds &B, const double *x, const double *g,
+// extrapolate by 10 while it holds and the path still moves.  Until the path
+// meets a bound, s(alpha) = -alpha g_P (g_P: g without the components pinned at
+// a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
+// once; trials past a breakpoint evaluate the projection in full.
+__device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x, const double *g,
                                        const double *H, double delta, double &alpha, double *s,
                                        Cnt &c)
 {
+    bool path[6];
+    double room[6], gp[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const bool gp_pos = dpos(g[i]);
+        path[i] = (gp_pos && B.above_lo(i, x[i])) || (dneg(g[i]) && B.below_hi(i, x[i]));
+        room[i] = gp_pos ? x[i] - B.lo(i) : B.hi(i) - x[i];
+        gp[i] = path[i] ? g[i] : 0.0;
+    }
+    double hg[6];
+    hmul(H, gp, hg);
+    const double G2 = dot6(gp, gp), GHG = dot6(gp, hg);
     const double d2 = delta * delta;
+    // sufficient decrease and radius test at alpha = a (uniform across the warp)
+    auto ok_at = [&](double a, bool need) -> bool {
+        bool unc = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) unc = unc && (!path[i] || dle(a * dabsi(g[i]), room[i]));
+        const double gs = -a * G2;
+        bool ok = dle(a * a * G2, d2) && dle(gs + 0.5 * a * a * GHG, kMu0 * gs);
+        if (__any_sync(kFull, need && !unc)) {
+            double t[6];
+            pstep(B, x, g, a, t);
+            const bool okf = cauchy_ok(g, H, t, d2);
+            ok = unc ? ok : okf;
+        }
+        return ok;
+    };
     double a = alpha;
-    pstep(B, x, g, a, s);
-    c.cauchy++;
-    const bool back = !cauchy_ok(g, H, s, d2);
-    bool go = true;
+    if (on) c.cauchy++;
+    const bool back = !ok_at(a, on);
+    bool go = on;
     for (int t = 0; t < kCauchyTrials; ++t) {
-        if (!back) {
-            // stop once a is at or past every breakpoint of the projected path,
-            // i.e. a g_i >= x_i - l_i (g_i > 0) and a g_i <= x_i - u_i (g_i < 0)
+        if (go && !back) {
+            // the path stops moving once a is past every breakpoint
             bool past = true;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                if (g[i] > 0.0 && x[i] > B.lo(i)) past = past && a * g[i] >= x[i] - B.lo(i);
-                else if (g[i] < 0.0 && x[i] < B.hi(i)) past = past && a * g[i] <= x[i] - B.hi(i);
-            }
-            if (past) go = false;
+            for (int i = 0; i < 6; ++i) past = past && (!path[i] || dle(room[i], a * dabsi(g[i])));
+            go = !past;
         }
-        if (!go) break;
+        if (!__any_sync(kFull, go)) break;
         const double an = back ? a * 0.1 : a * 10.0;
-        double sn[6];
-        pstep(B, x, g, an, sn);
-        c.cauchy++;
-        const bool ok = cauchy_ok(g, H, sn, d2);
-        if (back || ok) {
-            a = an;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) s[i] = sn[i];
-        }
+        if (go) c.cauchy++;
+        const bool ok = ok_at(an, go);
+        if (go && (back || ok)) a = an;
         if (ok == back) go = false;    // backtracking found a point / extrapolation failed
     }
-    alpha = a;
+    pstep(B, x, g, a, s);
+    if (on) alpha = a;
 }
 
 __device__ __forceinline__ double boundary_tau(const double *a, const double *pv, double delta)
 {
     const double pp = dot6(pv, pv), ap = dot6(a, pv), aa = dot6(a, a);
-    const double rad = fmax(delta * delta - aa, 0.0);
+    const double rad = dmaxi(delta * delta - aa, 0.0);
     const double disc = sqrt(ap * ap + pp * rad);
-    if (pp == 0.0) return 0.0;
-    return ap > 0.0 ? rad / (ap + disc) : (disc - ap) / pp;
+    if (!dpos(pp)) return 0.0;
+    return dpos(ap) ? rad / (ap + disc) : (disc - ap) / pp;
 }
 
-// Preconditioner: Cholesky factor of D^-1 A D^-1 + sigma I on the free block
-// (identity on fixed variables), D = diag(sqrt|A_ii|).  Keeps 1/D and, on the
-// diagonal of L, the reciprocal pivots, so the solves only multiply.
-__device__ __forceinline__ bool chol_plain(const double *H, const bool *fr, double *L)
+// one Cholesky pass of D^-1 A D^-1 + sigma I on the free block (identity on
+// fixed variables); the diagonal of L keeps the reciprocal pivots.  Lanes
+// with keep == true leave L unchanged.
+__device__ __forceinline__ bool chol_pass(const double *H, const bool *fr, const double *dinv,
+                                          double sigma, bool keep, double *L)
 {
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double dd = fr[j] ? H[P(j, j)] : 1.0;
+        double dd = fr[j] ? H[P(j, j)] * dinv[j] * dinv[j] + sigma : 1.0;
 #pragma unroll
         for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
-        ok = ok && (dd > 0.0);
-        const double linv = rsqrt(fmax(dd, 1e-300));
-        L[P(j, j)] = linv;
+        ok = ok && dpos(dd);
+        const double linv = rsqrt(dmaxi(dd, 1e-300));
+        L[P(j, j)] = keep ? L[P(j, j)] : linv;
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            double v = (fr[i] && fr[j]) ? H[P(i, j)] : 0.0;
+            double v = (fr[i] && fr[j]) ? H[P(i, j)] * dinv[i] * dinv[j] : 0.0;
 #pragma unroll
             for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
-            L[P(i, j)] = v * linv;
+            L[P(i, j)] = keep ? L[P(i, j)] : v * linv;
         }
     }
     return ok;
 }
 
-__device__ __forceinline__ void precond_factor(const double *H, const bool *fr, double *L,
+// Preconditioner: Cholesky factor of D^-1 A D^-1 + sigma I on the free block,
+// D = diag(sqrt|A_ii|), sigma = 0 if every free A_ii > 0 else 1e-3, doubled
+// until the factorisation succeeds (at most kCholTries passes).  A positive
+// definite block is first factored unscaled: then D L L' D = L0 L0' exactly,
+// so the preconditioned CG iterates are the same.
+__device__ __forceinline__ void precond_factor(bool on, const double *H, const bool *fr, double *L,
                                                double *dinv)
 {
-    // A positive definite free block is factored as is: D L L' D with D the
-    // diagonal scaling equals L L' exactly then, so the preconditioned CG
-    // iterates are the same.  Otherwise scale and shift.
 #pragma unroll
     for (int i = 0; i < 6; ++i) dinv[i] = 1.0;
-    if (chol_plain(H, fr, L)) return;
+    const bool plain = chol_pass(H, fr, dinv, 0.0, false, L);
+    bool need = on && !plain;
+    if (!__any_sync(kFull, need)) return;
     bool pos = true;
+    double ds[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const double a = H[P(i, i)];
-        dinv[i] = (fr[i] && a != 0.0) ? rsqrt(fabs(a)) : 1.0;
-        pos = pos && (!fr[i] || a > 0.0);
+        ds[i] = (fr[i] && okey(a) != 0) ? rsqrt(dabsi(a)) : 1.0;
+        pos = pos && (!fr[i] || dpos(a));
     }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dinv[i] = need ? ds[i] : dinv[i];
     double sigma = pos ? 0.0 : 1e-3;
     for (int tries = 0; tries < kCholTries; ++tries) {
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            double dd = fr[j] ? H[P(j, j)] * dinv[j] * dinv[j] + sigma : 1.0;
-#pragma unroll
-            for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
-            ok = ok && (dd > 0.0);
-            const double linv = rsqrt(fmax(dd, 1e-300));
-            L[P(j, j)] = linv;
-#pragma unroll
-            for (int i = j + 1; i < 6; ++i) {
-                double v = (fr[i] && fr[j]) ? H[P(i, j)] * dinv[i] * dinv[j] : 0.0;
-#pragma unroll
-                for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
-                L[P(i, j)] = v * linv;
-            }
-        }
-        if (ok) return;
-        sigma = fmax(sigma * 2.0, 1e-3);
+        if (!__any_sync(kFull, need)) break;
+        const bool ok = chol_pass(H, fr, dinv, sigma, !need, L);
+        need = need && !ok;
+        sigma = dmaxi(sigma * 2.0, 1e-3);
     }
+    if (__any_sync(kFull, need)) {   // give up: identity in the scaled space
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < 6; ++i) {
 #pragma unroll
-        for (int j = 0; j <= i; ++j) L[P(i, j)] = (i == j) ? 1.0 : 0.0;
+            for (int j = 0; j <= i; ++j) L[P(i, j)] = need ? ((i == j) ? 1.0 : 0.0) : L[P(i, j)];
+        }
     }
 }
 
@@ -372,7 +439,7 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
-__device__ __forceinline__ void subspace(const Bounds &B, const double *x, const double *g,
+__device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
                                          const double *H, double delta, const double *sc,
                                          double *s, Cnt &c)
 {
@@ -382,17 +449,18 @@ __device__ __forceinline__ void subspace(const Bounds &B, const double *x, const
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         xc[i] = x[i] + sc[i];
-        fr[i] = xc[i] > B.lo(i) && xc[i] < B.hi(i);
+        fr[i] = B.above_lo(i, xc[i]) && B.below_hi(i, xc[i]);
         any = any || fr[i];
         s[i] = sc[i];
     }
-    if (!any) return;
+    const bool act = on && any;
+    if (!__any_sync(kFull, act)) return;
     double gc[6];
     hmul(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
     double L[21], dinv[6];
-    precond_factor(H, fr, L, dinv);
+    precond_factor(act, H, fr, L, dinv);
     double w[6], r[6], z[6], pv[6], q[6];
     double rn0 = 0.0;
 #pragma unroll
@@ -401,7 +469,8 @@ __device__ __forceinline__ void subspace(const Bounds &B, const double *x, const
         r[i] = fr[i] ? -gc[i] : 0.0;
         rn0 += r[i] * r[i];
     }
-    if (rn0 == 0.0) return;
+    const bool cgon = act && dpos(rn0);
+    if (!__any_sync(kFull, cgon)) return;
     precond_solve(L, dinv, r, z);
     double rz = 0.0;
 #pragma unroll
@@ -411,8 +480,10 @@ __device__ __forceinline__ void subspace(const Bounds &B, const double *x, const
     }
     const double tol2 = kCgRtol * kCgRtol * rn0;
     const double d2 = delta * delta;
+    bool go = cgon;
     for (int it = 0; it < kCgMaxit; ++it) {
-        c.cg++;
+        if (!__any_sync(kFull, go)) break;
+        if (go) c.cg++;
         hmul(H, pv, q);
         double kappa = 0.0;
 #pragma unroll
@@ -430,20 +501,23 @@ __device__ __forceinline__ void subspace(const Bounds &B, const double *x, const
             const double v = cur[i] + al * pv[i];
             nx2 += v * v;
         }
-        if (kappa <= 0.0 || nx2 >= d2) {   // negative curvature or trust-region boundary
+        // negative curvature or the trust-region boundary: stop on the boundary
+        const bool bnd = go && (!dpos(kappa) || dle(d2, nx2));
+        if (__any_sync(kFull, bnd)) {
             const double tau = boundary_tau(cur, pv, delta);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) w[i] += tau * pv[i];
-            break;
+            for (int i = 0; i < 6; ++i) w[i] = bnd ? w[i] + tau * pv[i] : w[i];
         }
+        go = go && !bnd;
         double rn = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            w[i] += al * pv[i];
-            r[i] -= al * q[i];
+            w[i] = go ? w[i] + al * pv[i] : w[i];
+            r[i] = go ? r[i] - al * q[i] : r[i];
             rn += r[i] * r[i];
         }
-        if (rn <= tol2) break;
+        go = go && !dle(rn, tol2);
+        if (!__any_sync(kFull, go)) break;
         precond_solve(L, dinv, r, z);
         double rz1 = 0.0;
 #pragma unroll
@@ -452,25 +526,26 @@ __device__ __forceinline__ void subspace(const Bounds &B, const double *x, const
             rz1 += r[i] * z[i];
         }
         const double be = rz1 / rz;
-        rz = rz1;
+        rz = go ? rz1 : rz;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) pv[i] = z[i] + be * pv[i];
+        for (int i = 0; i < 6; ++i) pv[i] = go ? z[i] + be * pv[i] : pv[i];
     }
     const double qc = qmodel(g, H, sc);
     double beta = 1.0;
+    bool ps = cgon;
     for (int t = 0; t < kPsTrials; ++t) {
-        c.ps++;
+        if (!__any_sync(kFull, ps)) break;
+        if (ps) c.ps++;
         double sb[6], dd[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            sb[i] = clampd(xc[i] + beta * w[i], B.lo(i), B.hi(i)) - x[i];
+            sb[i] = B.clamp(i, xc[i] + beta * w[i]) - x[i];
             dd[i] = sb[i] - sc[i];
         }
-        if (qmodel(g, H, sb) <= qc + kMu0 * dot6(gc, dd)) {
+        const bool okp = ps && dle(qmodel(g, H, sb), qc + kMu0 * dot6(gc, dd));
 #pragma unroll
-            for (int i = 0; i < 6; ++i) s[i] = sb[i];
-            return;
-        }
+        for (int i = 0; i < 6; ++i) s[i] = okp ? sb[i] : s[i];
+        ps = ps && !okp;
         beta *= 0.5;
     }
 }
@@ -509,7 +584,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
 
     int b = -1, state = LS_IDLE, apass = 0, k = 0, trips = 0;
     bool exhausted = false;
-    Bounds B{1.0, 1.0, 1.0, 1.0, 0.0};
+    Bounds B{1.0, 1.0, 1.0, 1.0, 0.0, 0, 0, 0, 0, 0};
     double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xt[6], g[6], H[21], F[4] = {0.0, 0.0, 0.0, 0.0};
     double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0, prered = 0.0, snorm = 0.0;
     double lt0 = 0.0, lt1 = 0.0, rt = rt0, hprev = 0.0;
@@ -517,33 +592,39 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     while (true) {
         bool eval = false;
         // (T) one TRON iteration up to its trial point, or the stop of the solve
+        bool go_t = false;
         if (state == LS_ITER) {
             if (k >= O.tron_max_iter) {
                 c.maxhit++;
                 state = LS_DONE;
-            } else if (pgnorm(B, x, g) <= gtol) {
+            } else if (dle(pgnorm(B, x, g), gtol)) {
                 state = LS_DONE;
             } else {
                 c.tron_iters++;
-                double sc[6], s[6];
-                cauchy(B, x, g, H, delta, alpha, sc, c);
-                subspace(B, x, g, H, delta, sc, s, c);
+                go_t = true;
+            }
+        }
+        if (__any_sync(kFull, go_t)) {
+            double sc[6], s[6];
+            cauchy(go_t, B, x, g, H, delta, alpha, sc, c);
+            subspace(go_t, B, x, g, H, delta, sc, s, c);
+            if (go_t) {
                 double xn = 0.0, sn = 0.0;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
-                    xn = fmax(xn, fabs(x[i]));
-                    sn = fmax(sn, fabs(s[i]));
+                    xn = amax(xn, x[i]);
+                    sn = amax(sn, s[i]);
                 }
-                if (sn <= O.tron_xtol * fmax(xn, 1.0)) {
+                if (dle(sn, O.tron_xtol * dmaxi(xn, 1.0))) {
                     state = LS_DONE;
                 } else {
                     prered = -qmodel(g, H, s);
                     c.f++;
-                    if (prered <= 0.0) {
+                    if (!dpos(prered)) {
                         state = LS_DONE;          // no decrease predicted: stalled
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 6; ++i) xt[i] = clampd(x[i] + s[i], B.lo(i), B.hi(i));
+                        for (int i = 0; i < 6; ++i) xt[i] = B.clamp(i, x[i] + s[i]);
                         snorm = sqrt(dot6(s, s));
                         eval = true;
                     }
@@ -558,10 +639,10 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             const double h1 = F[2] * F[2] + F[3] * F[3] + x[5];
             lt0 += rt * h0;
             lt1 += rt * h1;
-            const double hm = fmax(fabs(h0), fabs(h1));
-            bool fin = hm <= O.al_tol;
+            const double hm = amax(dabsi(h0), h1);
+            bool fin = dle(hm, O.al_tol);
             if (!fin) {
-                if (hm > O.al_decay * hprev) rt = fmin(rt * O.al_rho_factor, O.al_rho_max);
+                if (dlt(O.al_decay * hprev, hm)) rt = dmini(rt * O.al_rho_factor, O.al_rho_max);
                 hprev = hm;
                 fin = apass >= O.al_max_iter;
             }
@@ -623,6 +704,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                     B.vlo_j = G.lim[2 * nl + b];
                     B.vhi_j = G.lim[3 * nl + b];
                     B.slo = G.lim[4 * nl + b];
+                    B.set_keys();
 #pragma unroll
                     for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
                     lt0 = G.blt[b];
@@ -644,7 +726,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             c.al++;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                x[i] = clampd(x[i], B.lo(i), B.hi(i));
+                x[i] = B.clamp(i, x[i]);
                 xt[i] = x[i];
             }
             eval = true;
@@ -662,7 +744,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             f = fe;
             c.tron_calls++;
             c.fgh++;
-            gtol = O.tron_gtol * fmax(pgnorm(B, x, g), 1.0);
+            gtol = O.tron_gtol * dmaxi(pgnorm(B, x, g), 1.0);
             double sp[6];
             pstep(B, x, g, 1.0, sp);
             delta = sqrt(dot6(sp, sp));
@@ -673,12 +755,12 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             state = LS_ITER;
         } else if (state == LS_ITER && eval) {
             const double actred = f - fe;
-            if (k == 0 && snorm < delta) delta = snorm;
-            const double fa = fmax(fabs(f), 1.0);
-            const double ratio = prered <= O.tron_ftol * fa ? 1.0 : actred / prered;
-            if (ratio < kEta1) delta = kSigma1 * fmin(snorm, delta);
-            else if (ratio > kEta2) delta = fmax(delta, kSigma3 * snorm);
-            if (ratio > kEta0) {
+            if (k == 0 && dlt(snorm, delta)) delta = snorm;
+            const double fa = dmaxi(dabsi(f), 1.0);
+            const double ratio = dle(prered, O.tron_ftol * fa) ? 1.0 : actred / prered;
+            if (dlt(ratio, kEta1)) delta = kSigma1 * dmini(snorm, delta);
+            else if (dlt(kEta2, ratio)) delta = dmaxi(delta, kSigma3 * snorm);
+            if (dlt(kEta0, ratio)) {
 #pragma unroll
                 for (int i = 0; i < 6; ++i) x[i] = xt[i];
                 f = fe;
@@ -688,8 +770,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             }
             double xn = 0.0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) xn = fmax(xn, fabs(x[i]));
-            if (delta <= 1e-14 * fmax(xn, 1.0)) state = LS_DONE;
+            for (int i = 0; i < 6; ++i) xn = amax(xn, x[i]);
+            if (dle(delta, 1e-14 * dmaxi(xn, 1.0))) state = LS_DONE;
             ++k;
         }
     }
