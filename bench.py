@@ -26,17 +26,20 @@ METRIC = "ADMM iterations/s, 70k-bus synthetic grid"
 C_RESIDUALS_BYTES = 72   # sizeof(admm_residuals): 4 int32 + 7 double
 UNIT = "iter/s"
 
-# Algorithmic FP64 operations of the branch subproblem solver, counted from
-# the method's formulas (an FMA counts 2, sin and cos 1 each, comparisons and
-# min/max 0).  Multiplied by the per-solve counters the kernel reports.
+# Algorithmic FP64 operations of the branch subproblem solver, counted by
+# hand from the operations the method specifies (an FMA counts 2; add, mul,
+# div, sqrt, sin and cos 1 each; comparisons, min/max and projections 0).
+# Multiplied by the counters the kernel reports for one launch.
 FLOPS = dict(
-    fgh=268,        # flows + first/second derivatives + AL assembly of g and H
-    f=66,           # flows + function value
-    cauchy=103,     # projected step (12) + ||s|| (12) + q(s) (84) per trial, less shared
-    tron_iter=330,  # subspace: gc (72), scaled Cholesky (~110), PCG set-up, ratio test
-    cg=150,         # one PCG iteration: Hp (72), dots, TR test, preconditioner solve (~50)
-    ps=110,         # one projected-search trial: step (12) + q(s) (84) + descent test
-    al=34,          # one AL pass: flows at the solution + multiplier update
+    fgh=392,        # f, gradient and Hessian of eq. branch: flows and their
+                    # derivatives (80), coupling/AL accumulation (180), h-terms (54), rest
+    f=74,           # f alone at a trial point (flows, residuals, AL terms)
+    cauchy=103,     # one Cauchy trial: projected step (18), |s|^2 (12), q(s) (60), g's (12)
+    tron_iter=461,  # per TRON iteration besides trials/CG/search/evaluations: projected
+                    # gradient, breakpoints, g + H sc, scaled Cholesky, PCG set-up, ratio test
+    cg=254,         # one PCG iteration: H p (72), curvature, TR test, updates, M^-1 r (84)
+    ps=100,         # one projected-search trial: step (24), q(s) (60), descent test
+    al=13,          # one AL pass: h of both ends, multiplier and penalty update
 )
 
 
@@ -48,10 +51,10 @@ def algorithmic_flops(stats: dict) -> float:
 
 
 def fp64_peak_gflops():
-    """FP64 peak of a GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA
-    per clock per SM (measured FMA issue rate) x 2 flops x
-    2.07 GHz."""
-    return 152 * 2 * 2 * 2.070
+    """FP64 peak of a GB300 from unit counts and clock: 152 SMs x 4 sub-
+    partitions x 0.5 FP64 FMA per clock (one warp instruction per 64 cycles
+    per sub-partition, measured) x 2 flops x 2.07 GHz = 1,258.6 GFLOP/s."""
+    return 152 * 4 * 0.5 * 2 * 2.070
 
 
 class ClockSampler:
@@ -194,9 +197,11 @@ def run_ours(args):
     s = admm.Solver(grid, stream=stream, **opts)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # warm-up: cold start + W iterations
+    # warm-up: cold start + W iterations; the state after them is kept so that
+    # the end-to-end leg times exactly the same iterations
     s.solve(tol=0.0, max_iter=max(args.warmup, 3))
     torch.cuda.synchronize()
+    checkpoint = s.get_state()
     st0 = s.stats()
     stats_acc = {k: 0 for k in st0}
     branch_ms, iter_ms, bus_ms = [], [], []
@@ -228,9 +233,11 @@ def run_ours(args):
     achieved = flops_per_launch / (b_mean * 1e-3) / 1e9
     peak = fp64_peak_gflops()
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, over the same
+    # iterations (state restored to the end of the warm-up)
     pd = torch.tensor(grid.pd, dtype=torch.float64).pin_memory().numpy()
     qd = torch.tensor(grid.qd, dtype=torch.float64).pin_memory().numpy()
+    s.set_state(checkpoint)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -247,16 +254,19 @@ def run_ours(args):
     if args.time_to_tol:
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        st_code = s.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
+        s.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
         ev1.record(stream)
         torch.cuda.synchronize()
         r = s.residuals()
         sol = s.solution()
-        tt = {"tol": 1e-3, "seconds": ev0.elapsed_time(ev1) / 1e3, "iters": r["iters"],
+        secs = ev0.elapsed_time(ev1) / 1e3
+        tt = {"tol": 1e-3, "seconds": secs, "iters": r["iters"], "iters_per_s": r["iters"] / secs,
+              "outer_iters": r["outer_iters"],
               "status": admm.lib().admm_status_string(r["status"]).decode(),
-              "primal": r["primal"], "dual": r["dual"], "z_norm": r["z_norm"],
-              "objective": sol["objective"], "max_viol": sol["max_viol"]}
-        del st_code
+              "primal": r["primal"], "eps_pri": r["eps_pri"], "dual": r["dual"],
+              "eps_dual": r["eps_dual"], "z_norm": r["z_norm"],
+              "objective": sol["objective"], "max_viol": sol["max_viol"],
+              "graph_launches": 1}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -269,7 +279,7 @@ def run_ours(args):
                              "flops_per_launch": flops_per_launch},
                 "bus_dual_ms": sum(bus_ms) / len(bus_ms),
                 "branch_solves_per_s": value * grid.nbranch,
-                "e2e": e2e, "clocks": clocks, "gpu_launches": 2 * args.steps * ws,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * args.steps * ws,
                 "tron_stats_per_step": {k: v / args.steps for k, v in stats_acc.items()}}
         if tt is not None:
             line["time_to_tol"] = tt

@@ -82,7 +82,7 @@ typedef struct {
     double beta_max;       /* cap on beta (1e12)                                     */
     double lambda_max;     /* projection bound of the outer multiplier (1e12)        */
     double tol_in0;        /* inner tolerance at outer step k: max(tol, tol_in0 *    */
-    double tol_in_decay;   /*   tol_in_decay^k)  (0.1, 0.5)                          */
+    double tol_in_decay;   /*   tol_in_decay^k)  (1e-2, 0.5)                         */
     double al_rho0;        /* initial rho-tilde of a branch solve; <= 0: rho_pq     */
     double al_tol;         /* line-limit AL stops when max|h| <= al_tol (1e-8)       */
     double al_decay;       /* rho-tilde grows unless max|h| fell below this share (0.25) */
@@ -109,6 +109,8 @@ typedef struct {
     double z_norm;          /* ||z||_2                                               */
     double primal_z;        /* ||u - xbar + z||_2 (inner residual)                   */
     double beta;            /* current outer penalty                                 */
+    double eps_pri;         /* sqrt(m) tol + tol max(||u||, ||xbar||) (last iteration) */
+    double eps_dual;        /* sqrt(m) tol + tol ||y||                               */
     double objective;       /* generation cost at the last admm_get_solution        */
     double max_viol;        /* ||c(x)||_inf at the last admm_get_solution           */
 } admm_residuals;
@@ -140,9 +142,15 @@ int admm_set_gen_bounds(admm_handle *h, const double *pmin, const double *pmax);
 
 /* Algorithm 1.  warm_start = 0 re-initialises every variable (Section IV-B);
  * 1 keeps all primal, dual and penalty values (Section IV-C) and restarts only
- * the loop counters.  Stops with ADMM_OK when ||u - xbar||, ||rho dxbar|| and
- * ||z|| (two-level only) are all <= tol, else with ADMM_NOT_CONVERGED after
- * max_iter inner iterations or max_outer outer updates.  Blocks until done. */
+ * the loop counters.  The tests are the standard ADMM ones with absolute and
+ * relative tolerance tol (they loosen with the number m of couplings, as
+ * Section IV-B notes): stops with ADMM_OK when ||u - xbar|| <= eps_pri,
+ * ||rho dxbar|| <= eps_dual and (two-level only) ||z|| <= eps_pri, where
+ * eps_pri = sqrt(m) tol + tol max(||u||, ||xbar||) and
+ * eps_dual = sqrt(m) tol + tol ||y||; the inner loop ends when
+ * ||u - xbar + z|| and ||rho dxbar|| pass the same tests at tol_in.  Otherwise
+ * ADMM_NOT_CONVERGED after max_iter inner iterations or max_outer outer
+ * updates.  Blocks until done. */
 int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
                int32_t warm_start);
 /* Same, without waiting: the work is enqueued on the handle's stream; read the

@@ -71,7 +71,7 @@ def default_options(**kw) -> dict:
     parameters the paper leaves open."""
     o = dict(rho_pq=10.0, rho_va=1000.0, obj_scale=1.0, line_limit_frac=0.99,
              beta0=0.0, beta_factor=6.0, z_decay=0.8, beta_max=1e12, lambda_max=1e12,
-             tol_in0=0.1, tol_in_decay=0.5, al_rho0=0.0, al_tol=1e-8, al_decay=0.25,
+             tol_in0=1e-2, tol_in_decay=0.5, al_rho0=0.0, al_tol=1e-8, al_decay=0.25,
              al_rho_factor=10.0, al_rho_max=1e12, tron_gtol=1e-10, tron_ftol=1e-12, tron_xtol=1e-13,
              two_level=1, max_outer=20, max_inner=1000, al_max_iter=20, tron_max_iter=200,
              pad_=0)
@@ -174,10 +174,11 @@ class Oracle:
         return out
 
     def residuals(self) -> dict:
-        d = np.zeros(6)
+        d = np.zeros(9)
         i = np.zeros(4, dtype=np.int32)
         lib().ora_get_residuals(self.h, _ptr(d), _ptr(i))
         return dict(primal=d[0], dual=d[1], z_norm=d[2], primal_z=d[3], beta=d[4], tol_in=d[5],
+                    u_norm=d[6], xbar_norm=d[7], y_norm=d[8],
                     iters=int(i[0]), outer_iters=int(i[1]), status=int(i[2]),
                     total_iters=int(i[3]))
 

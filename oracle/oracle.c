@@ -531,6 +531,7 @@ struct ora {
     /* results */
     int iters, total_iters, status;
     double pri, pri_z, dual, zn;
+    double nu, nx, ny;          /* ||u||, ||xbar||, ||y|| of the last iteration */
     ora_stats st;
     double *hist;
     int nhist;
@@ -821,7 +822,7 @@ static void iterate(ora *p, int l0, int l1)
     update_generators(p);
     update_branches(p, l0, l1);
     update_buses(p);
-    double sp = 0.0, spz = 0.0, sd = 0.0, sz = 0.0;
+    double sp = 0.0, spz = 0.0, sd = 0.0, sz = 0.0, su = 0.0, sx = 0.0, sy = 0.0;
     for (int c = 0; c < m; ++c) {
         double r0 = p->u[c] - p->xbar[c];
         /* Algorithm 1 line 5: eq. qp-bound with (l, u) = (-inf, inf):
@@ -840,14 +841,31 @@ static void iterate(ora *p, int l0, int l1)
         spz += (r0 + p->z[c]) * (r0 + p->z[c]);
         sd += dx * dx;
         sz += p->z[c] * p->z[c];
+        su += p->u[c] * p->u[c];
+        sx += p->xbar[c] * p->xbar[c];
+        sy += p->y[c] * p->y[c];
     }
     free(xprev);
     p->pri = sqrt(sp); p->pri_z = sqrt(spz); p->dual = sqrt(sd); p->zn = sqrt(sz);
+    p->nu = sqrt(su); p->nx = sqrt(sx); p->ny = sqrt(sy);
     if (p->nhist < HIST_CAP) {
         double *h = &p->hist[4 * p->nhist++];
         h[0] = p->pri; h[1] = p->dual; h[2] = p->zn; h[3] = p->pri_z;
     }
 }
+
+/* Stopping tolerances (reading of "the termination conditions of SunSun21",
+ * Section IV-A, which loosen as the number of consensus constraints grows,
+ * Section IV-B): the standard ADMM test of Boyd et al. (2011, Sec. 3.3.1) with
+ * absolute and relative tolerance both equal to t,
+ *   eps_pri(t)  = sqrt(m) t + t max(||u||, ||xbar||),
+ *   eps_dual(t) = sqrt(m) t + t ||y||. */
+static double eps_pri(const ora *p, double t)
+{
+    double a = p->nu > p->nx ? p->nu : p->nx;
+    return sqrt((double)p->m) * t + t * a;
+}
+static double eps_dual(const ora *p, double t) { return sqrt((double)p->m) * t + t * p->ny; }
 
 /* Algorithm 1 line 8 (outer level, readings of this implementation):
  * lam <- Proj_[-lambda_max, lambda_max](lam + beta z); beta <- beta_factor beta
@@ -871,7 +889,8 @@ static void outer_update(ora *p, double tol)
 }
 
 /* Algorithm 1: repeat { inner ADMM until converged; outer update } until
- * ||z|| <= tol.  Returns 0 when primal, dual and ||z|| are all <= tol,
+ * ||z|| <= eps_pri(tol).  Returns 0 when ||u - xbar|| <= eps_pri(tol),
+ * ||rho dxbar|| <= eps_dual(tol) and ||z|| <= eps_pri(tol);
  * 1 when max_iter or max_outer is reached first, -3 on a non-finite residual.
  * warm_start = 0 reinitialises (Section IV-B); 1 keeps every primal, dual and
  * penalty value (Section IV-C) and restarts only the loop counters. */
@@ -889,13 +908,15 @@ int ora_solve(ora *p, double tol, int32_t max_iter, int32_t warm_start)
         p->iters++;
         p->total_iters++;
         if (!isfinite(p->pri) || !isfinite(p->dual) || !isfinite(p->zn)) { p->status = -3; break; }
-        if (p->pri <= tol && p->dual <= tol && (!p->o.two_level || p->zn <= tol)) {
+        double ep = eps_pri(p, tol), ed = eps_dual(p, tol);
+        if (p->pri <= ep && p->dual <= ed && (!p->o.two_level || p->zn <= ep)) {
             p->status = 0;
             break;
         }
         if (p->o.two_level) {
             p->inner++;
-            if ((p->pri_z <= p->tol_in && p->dual <= p->tol_in) || p->inner >= p->o.max_inner) {
+            if ((p->pri_z <= eps_pri(p, p->tol_in) && p->dual <= eps_dual(p, p->tol_in)) ||
+                p->inner >= p->o.max_inner) {
                 outer_update(p, tol);
                 if (p->outer >= p->o.max_outer) break;
             }
@@ -920,11 +941,13 @@ int ora_get(const ora *p, int32_t which, double *out)
     }
 }
 
-/* dres: pri, dual, zn, pri_z, beta, tol_in;  ires: iters, outer, status, total */
+/* dres: pri, dual, zn, pri_z, beta, tol_in, ||u||, ||xbar||, ||y||;
+ * ires: iters, outer, status, total */
 void ora_get_residuals(const ora *p, double *dres, int32_t *ires)
 {
     dres[0] = p->pri; dres[1] = p->dual; dres[2] = p->zn; dres[3] = p->pri_z;
     dres[4] = p->beta; dres[5] = p->tol_in;
+    dres[6] = p->nu; dres[7] = p->nx; dres[8] = p->ny;
     ires[0] = p->iters; ires[1] = p->outer; ires[2] = p->status; ires[3] = p->total_iters;
 }
 

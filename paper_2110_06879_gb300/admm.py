@@ -45,7 +45,8 @@ class admm_residuals(C.Structure):
     _fields_ = [("iters", C.c_int32), ("outer_iters", C.c_int32), ("status", C.c_int32),
                 ("tron_failures", C.c_int32), ("primal_res", C.c_double),
                 ("dual_res", C.c_double), ("z_norm", C.c_double), ("primal_z", C.c_double),
-                ("beta", C.c_double), ("objective", C.c_double), ("max_viol", C.c_double)]
+                ("beta", C.c_double), ("eps_pri", C.c_double), ("eps_dual", C.c_double),
+                ("objective", C.c_double), ("max_viol", C.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -194,7 +195,8 @@ class Solver:
         _check(lib().admm_get_residuals(self.h, C.byref(r)), "admm_get_residuals")
         d = r.as_dict()
         return dict(primal=d["primal_res"], dual=d["dual_res"], z_norm=d["z_norm"],
-                    primal_z=d["primal_z"], beta=d["beta"], iters=d["iters"],
+                    primal_z=d["primal_z"], beta=d["beta"], eps_pri=d["eps_pri"],
+                    eps_dual=d["eps_dual"], iters=d["iters"],
                     outer_iters=d["outer_iters"], status=d["status"],
                     tron_failures=d["tron_failures"], objective=d["objective"],
                     max_viol=d["max_viol"])

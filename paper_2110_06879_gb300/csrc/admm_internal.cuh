@@ -38,6 +38,7 @@ struct Ctrl {
     int32_t iter, inner, outer, status, done, pending, total_iters, pad0;
     double beta, beta_used, tol_in, zprev;
     double pri, dual, zn, pri_z;
+    double eps_pri, eps_dual;
     // finalize outputs
     double objective, max_viol;
     unsigned int counter;          // last-block detection of bus_dual
@@ -77,7 +78,7 @@ struct DevGrid {
     double *sx, *sz, *sy, *sl;
     // scratch and control
     int32_t *cls_list;             // [2][3][nl] branch ids per (parity, class)
-    double *partials;              // [nblk_bus][4]
+    double *partials;              // [nblk_bus][8]
     double *fin_partials;          // [nblk_fin][2]
     double *hist;                  // [kHistCap][4]
     Ctrl *ctrl;

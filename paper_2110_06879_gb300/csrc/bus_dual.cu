@@ -198,7 +198,7 @@ __global__ void begin_kernel(DevGrid G, DevOpts O, SolveParams P)
 __global__ void __launch_bounds__(kBusBlock)
 bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t use_cond)
 {
-    __shared__ double sh[kBusBlock / 32][4];
+    __shared__ double sh[kBusBlock / 32][7];
     __shared__ bool last;
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) {
@@ -212,7 +212,8 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     const bool pending = ctrl->pending != 0;
     const double bused = ctrl->beta_used, lmax = O.lambda_max;
     const bool two = O.two_level != 0;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // |u-xbar|^2, |u-xbar+z|^2, |rho dxbar|^2, |z|^2
+    // |u-xbar|^2, |u-xbar+z|^2, |rho dxbar|^2, |z|^2, |u|^2, |xbar|^2, |y|^2
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (i < nb) {
         const int r0 = G.row_ptr[i], r1 = G.row_ptr[i + 1];
         const double so = O.obj_scale;
@@ -317,6 +318,9 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
                 acc[1] += (r0c + zn) * (r0c + zn);
                 acc[2] += dual * dual;
                 acc[3] += zn * zn;
+                acc[4] += u[c] * u[c];
+                acc[5] += xb * xb;
+                acc[6] += yn * yn;
                 if (isb) {
                     // component index in bt: from end {0,1,4,5}, to end {2,3,6,7}
                     const int comp = (c < 2 ? c : c + 2) + (end ? 2 : 0);
@@ -325,10 +329,10 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
             }
         }
     }
-    block_sum<kBusBlock, 4>(acc, sh);
+    block_sum<kBusBlock, 7>(acc, sh);
     if (threadIdx.x == 0) {
-        double *pp = G.partials + 4 * blockIdx.x;
-        pp[0] = acc[0]; pp[1] = acc[1]; pp[2] = acc[2]; pp[3] = acc[3];
+        double *pp = G.partials + 8 * blockIdx.x;
+        for (int k = 0; k < 7; ++k) pp[k] = acc[k];
         __threadfence();
         unsigned int ticket = atomicAdd(&ctrl->counter, 1u);
         last = ticket == gridDim.x - 1;
@@ -337,18 +341,25 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     if (!last) return;
     __threadfence();
     // last block: fixed-order sum of the block partials
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        const volatile double *pp = G.partials + 4 * b;
-        v[0] += pp[0]; v[1] += pp[1]; v[2] += pp[2]; v[3] += pp[3];
+        const volatile double *pp = G.partials + 8 * b;
+        for (int k = 0; k < 7; ++k) v[k] += pp[k];
     }
-    block_sum<kBusBlock, 4>(v, sh);
+    block_sum<kBusBlock, 7>(v, sh);
     if (threadIdx.x != 0) return;
     Ctrl *c = ctrl;
     c->counter = 0;
     c->branch_next = 0;     // the next branch_tron launch starts its queue at 0
     const double pri = sqrt(v[0]), pri_z = sqrt(v[1]), dual = sqrt(v[2]), zn = sqrt(v[3]);
     c->pri = pri; c->pri_z = pri_z; c->dual = dual; c->zn = zn;
+    // standard ADMM tolerances (absolute and relative both t):
+    // eps_pri(t) = sqrt(m) t + t max(|u|, |xbar|), eps_dual(t) = sqrt(m) t + t |y|
+    const double sqm = sqrt((double)(2 * ng + 8 * nl));
+    const double nux = fmax(sqrt(v[4]), sqrt(v[5])), ny = sqrt(v[6]);
+    const double ep = sqm * c->tol + c->tol * nux, ed = sqm * c->tol + c->tol * ny;
+    c->eps_pri = ep;
+    c->eps_dual = ed;
     double *h = G.hist + 4 * (c->iter % kHistCap);
     h[0] = pri; h[1] = dual; h[2] = zn; h[3] = pri_z;
     c->iter += 1;
@@ -364,13 +375,15 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     if (!isfinite(pri) || !isfinite(dual) || !isfinite(zn)) {
         c->status = -3;
         stop = 1;
-    } else if (pri <= c->tol && dual <= c->tol && (!two || zn <= c->tol)) {
+    } else if (pri <= ep && dual <= ed && (!two || zn <= ep)) {
         c->status = 0;
         stop = 1;
     } else {
         if (two) {
             c->inner += 1;
-            if ((pri_z <= c->tol_in && dual <= c->tol_in) || c->inner >= O.max_inner) {
+            const double epi = sqm * c->tol_in + c->tol_in * nux;
+            const double edi = sqm * c->tol_in + c->tol_in * ny;
+            if ((pri_z <= epi && dual <= edi) || c->inner >= O.max_inner) {
                 // outer step: lambda <- Proj(lambda + beta z) (applied lazily),
                 // beta grows when ||z|| stalled
                 c->pending = 1;

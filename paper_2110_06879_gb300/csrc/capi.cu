@@ -80,7 +80,7 @@ extern "C" void admm_default_options(admm_options *o)
     o->z_decay = 0.8;
     o->beta_max = 1e12;
     o->lambda_max = 1e12;
-    o->tol_in0 = 0.1;
+    o->tol_in0 = 1e-2;
     o->tol_in_decay = 0.5;
     o->al_rho0 = 0.0;
     o->al_tol = 1e-8;
@@ -325,7 +325,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
     size_t o_sy = cv.take<double>(4 * (size_t)ns), o_sl = cv.take<double>(4 * (size_t)ns);
     size_t o_cls = cv.take<int32_t>(6 * (size_t)nl);
-    size_t o_part = cv.take<double>(4 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
+    size_t o_part = cv.take<double>(8 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
     size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
     size_t o_ctrl = cv.take<Ctrl>(1);
     size_t o_out = cv.take<double>(2 * (size_t)nb + 4 * (size_t)nl + 2 * (size_t)ng + 1);
@@ -549,6 +549,8 @@ extern "C" int admm_get_residuals(admm_handle *h, admm_residuals *out)
     out->z_norm = c.zn;
     out->primal_z = c.pri_z;
     out->beta = c.beta;
+    out->eps_pri = c.eps_pri;
+    out->eps_dual = c.eps_dual;
     out->objective = h->last_obj;
     out->max_viol = h->last_viol;
     return ADMM_OK;

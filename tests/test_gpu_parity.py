@@ -95,8 +95,8 @@ def test_converged_solve_matches_oracle():
     grid = synth.tiny_grid(0)
     s = admm.Solver(grid, **TINY)
     o = oracle.Oracle(grid, **TINY)
-    st_o = o.solve(tol=1e-4, max_iter=20000)
-    st_g = s.solve(tol=1e-4, max_iter=20000)
+    st_o = o.solve(tol=1e-7, max_iter=20000)
+    st_g = s.solve(tol=1e-7, max_iter=20000)
     assert st_o == st_g == admm.ADMM_OK
     sol, solo = s.solution(), o.finalize()
     assert abs(sol["objective"] - solo["objective"]) <= 1e-6 * abs(solo["objective"])

@@ -282,7 +282,7 @@ def test_z_and_y_updates(oracle_mod):
     """Line 5-6 of Algorithm 1: z is the stationary point of
     lam z + beta/2 z^2 + y (r0 + z) + rho/2 (r0 + z)^2; y += rho (r0 + z)."""
     grid = synth.tiny_grid(2)
-    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5)
+    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5, tol_in0=1e-12)   # no outer step yet
     a = oracle_mod.Oracle(grid, **kw); a.solve(tol=0.0, max_iter=3)
     b = oracle_mod.Oracle(grid, **kw); b.solve(tol=0.0, max_iter=4)
     assert b.residuals()["outer_iters"] == 0
@@ -356,10 +356,11 @@ def test_tiny_admm_solves_acopf(oracle_mod):
     eq. acopf to 1e-4 relative; it is no worse than the built-in point."""
     grid = synth.tiny_grid(0)
     o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4, beta0=1e5)
-    status = o.solve(tol=1e-4, max_iter=20000)
+    status = o.solve(tol=1e-7, max_iter=20000)
     res = o.residuals()
     assert status == 0, res
-    assert res["z_norm"] <= 1e-4
+    m = 2 * grid.ngen + 8 * grid.nbranch
+    assert res["z_norm"] <= np.sqrt(m) * 1e-7 + 1e-7 * max(res["u_norm"], res["xbar_norm"])
     sol = o.finalize()
     mis = mismatch(sol["vm"], sol["va"], sol["pg"], sol["qg"], grid)
     assert np.abs(mis).max() <= 1e-4
