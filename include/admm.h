@@ -140,6 +140,13 @@ int admm_set_loads_device(admm_handle *h, const double *d_pd, const double *d_qd
  * limits around the previous dispatch when tracking (Section IV-C). */
 int admm_set_gen_bounds(admm_handle *h, const double *pmin, const double *pmax);
 
+/* Ramp limit of Section IV-C for the next solve: the generator real-power
+ * bounds become [max(pmin, pg - frac pmax), min(pmax, pg + frac pmax)] around
+ * the current dispatch pg (on the device), where pmin, pmax are the bounds last
+ * given to admm_create or admm_set_gen_bounds (the paper uses frac = 0.02).
+ * The next admm_set_gen_bounds replaces them.  Ordered on the handle's stream. */
+int admm_set_ramp_limit(admm_handle *h, double frac);
+
 /* Algorithm 1.  warm_start = 0 re-initialises every variable (Section IV-B);
  * 1 keeps all primal, dual and penalty values (Section IV-C) and restarts only
  * the loop counters.  The tests are the standard ADMM ones with absolute and

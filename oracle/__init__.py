@@ -95,6 +95,8 @@ def lib():
         L.ora_destroy.argtypes = [vp]
         L.ora_cold_start.argtypes = [vp]
         L.ora_set_loads.argtypes = [vp, vp, vp]
+        L.ora_set_gen_bounds.argtypes = [vp, vp, vp]
+        L.ora_set_ramp_limit.argtypes = [vp, d]
         L.ora_solve.argtypes = [vp, d, i32, i32]
         L.ora_solve.restype = C.c_int
         L.ora_get.argtypes = [vp, i32, vp]
@@ -166,6 +168,14 @@ class Oracle:
         pd = np.ascontiguousarray(pd, dtype=np.float64)
         qd = np.ascontiguousarray(qd, dtype=np.float64)
         lib().ora_set_loads(self.h, _ptr(pd), _ptr(qd))
+
+    def set_gen_bounds(self, pmin, pmax):
+        pmin = np.ascontiguousarray(pmin, dtype=np.float64)
+        pmax = np.ascontiguousarray(pmax, dtype=np.float64)
+        lib().ora_set_gen_bounds(self.h, _ptr(pmin), _ptr(pmax))
+
+    def set_ramp_limit(self, frac=0.02):
+        lib().ora_set_ramp_limit(self.h, frac)
 
     def get(self, which: int) -> np.ndarray:
         n = {BRANCH_X: 6 * self.nl, BRANCH_LT: 2 * self.nl, BUS: 2 * self.nb}.get(which, self.m)

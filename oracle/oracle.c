@@ -522,6 +522,7 @@ struct ora {
     double *rate, *Y;
     int *gb;
     double *pmin, *pmax, *qmin, *qmax, *c2, *c1, *c0;   /* c2, c1 per unit */
+    double *pbase_lo, *pbase_hi;                          /* bounds set by the caller */
     ora_options o;
     int *row, *col;
     /* state */
@@ -571,6 +572,7 @@ ora *ora_create(const ora_grid *g, const ora_options *o)
         ora_admittance(g->r[l], g->x[l], g->b[l], g->tap[l], g->shift[l], &p->Y[8 * l]);
     p->gb = dup_i(g->gen_bus, p->ng);
     p->pmin = dup_d(g->pmin, p->ng); p->pmax = dup_d(g->pmax, p->ng);
+    p->pbase_lo = dup_d(g->pmin, p->ng); p->pbase_hi = dup_d(g->pmax, p->ng);
     p->qmin = dup_d(g->qmin, p->ng); p->qmax = dup_d(g->qmax, p->ng);
     p->c2 = dup_d(NULL, p->ng); p->c1 = dup_d(NULL, p->ng); p->c0 = dup_d(g->c0, p->ng);
     /* costs to per-unit power: c2' = c2 base^2, c1' = c1 base (MATPOWER units) */
@@ -612,6 +614,7 @@ ora *ora_create(const ora_grid *g, const ora_options *o)
 void ora_destroy(ora *p)
 {
     if (!p) return;
+    free(p->pbase_lo); free(p->pbase_hi);
     double *d[] = {p->pd, p->qd, p->gs, p->bs, p->vmin, p->vmax, p->rate, p->Y, p->pmin,
                    p->pmax, p->qmin, p->qmax, p->c2, p->c1, p->c0, p->u, p->xbar, p->z,
                    p->y, p->lam, p->rho, p->bx, p->lt, p->bus, p->hist};
@@ -689,6 +692,28 @@ int ora_set_loads(ora *p, const double *pd, const double *qd)
     memcpy(p->pd, pd, sizeof(double) * p->nb);
     memcpy(p->qd, qd, sizeof(double) * p->nb);
     return 0;
+}
+
+int ora_set_gen_bounds(ora *p, const double *pmin, const double *pmax)
+{
+    memcpy(p->pmin, pmin, sizeof(double) * p->ng);
+    memcpy(p->pmax, pmax, sizeof(double) * p->ng);
+    memcpy(p->pbase_lo, pmin, sizeof(double) * p->ng);
+    memcpy(p->pbase_hi, pmax, sizeof(double) * p->ng);
+    return 0;
+}
+
+/* Section IV-C ramp limit |p_{t+1} - p_t| <= frac * pmax around the current
+ * dispatch, on the bounds last set by the caller (lower kept <= upper). */
+void ora_set_ramp_limit(ora *p, double frac)
+{
+    for (int k = 0; k < p->ng; ++k) {
+        double pg = p->u[2 * k], r = frac * p->pbase_hi[k];
+        double hi = pg + r < p->pbase_hi[k] ? pg + r : p->pbase_hi[k];
+        double lo = pg - r > p->pbase_lo[k] ? pg - r : p->pbase_lo[k];
+        p->pmin[k] = lo < hi ? lo : hi;
+        p->pmax[k] = hi;
+    }
 }
 
 /* Algorithm 1 line 3, generators: eq. qp-bound with the scaled cost */

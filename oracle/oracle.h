@@ -70,6 +70,8 @@ ora *ora_create(const ora_grid *g, const ora_options *o);
 void ora_destroy(ora *p);
 void ora_cold_start(ora *p);
 int ora_set_loads(ora *p, const double *pd, const double *qd);
+int ora_set_gen_bounds(ora *p, const double *pmin, const double *pmax);
+void ora_set_ramp_limit(ora *p, double frac);
 int ora_solve(ora *p, double tol, int32_t max_iter, int32_t warm_start);
 int ora_get(const ora *p, int32_t which, double *out);
 void ora_get_residuals(const ora *p, double *dres, int32_t *ires);

@@ -71,6 +71,7 @@ def lib():
             "admm_set_loads": (C.c_int, [vp, vp, vp]),
             "admm_set_loads_device": (C.c_int, [vp, vp, vp]),
             "admm_set_gen_bounds": (C.c_int, [vp, vp, vp]),
+            "admm_set_ramp_limit": (C.c_int, [vp, d]),
             "admm_solve": (C.c_int, [vp, d, d, d, i32, i32]),
             "admm_solve_async": (C.c_int, [vp, d, d, d, i32, i32]),
             "admm_get_solution": (C.c_int, [vp] + [vp] * 8),
@@ -177,6 +178,9 @@ class Solver:
         pmin = np.ascontiguousarray(pmin, dtype=np.float64)
         pmax = np.ascontiguousarray(pmax, dtype=np.float64)
         _check(lib().admm_set_gen_bounds(self.h, _ptr(pmin), _ptr(pmax)), "admm_set_gen_bounds")
+
+    def set_ramp_limit(self, frac=0.02):
+        _check(lib().admm_set_ramp_limit(self.h, frac), "admm_set_ramp_limit")
 
     def solve(self, tol=1e-4, max_iter=5000, warm_start=False, rho_pq=None, rho_va=None) -> int:
         rp = self.opts.rho_pq if rho_pq is None else rho_pq

@@ -71,6 +71,7 @@ struct DevGrid {
     // generators
     const int32_t *gen_bus;
     double *gc, *glim, *gu;
+    double *gbase;                 // [2][ng] pmin, pmax as last set by the caller
     // buses
     double *bus, *bw, *bth;
     const int32_t *row_ptr, *col;
@@ -98,6 +99,7 @@ __global__ void branch_tron_kernel(DevGrid G, DevOpts O);
 __global__ void bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond,
                                 int32_t use_cond);
 __global__ void flush_lambda_kernel(DevGrid G, DevOpts O);
+__global__ void ramp_limit_kernel(DevGrid G, double frac);
 __global__ void finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va,
                                 double *pf, double *qf, double *pt, double *qt, int32_t nblk);
 

@@ -408,6 +408,21 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
     if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
+// Ramp limit of Section IV-C around the current dispatch pg:
+// pmin' = max(pmin, pg - frac pmax), pmax' = min(pmax, pg + frac pmax) on the
+// bounds last set by the caller (pmin' kept <= pmax').
+__global__ void ramp_limit_kernel(DevGrid G, double frac)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ng = G.ng;
+    if (g >= ng) return;
+    const double lo = G.gbase[g], hi = G.gbase[ng + g], pg = G.gu[g];
+    const double r = frac * hi;
+    const double nhi = fmin(hi, pg + r);
+    G.glim[g] = fmin(fmax(lo, pg - r), nhi);
+    G.glim[ng + g] = nhi;
+}
+
 // After the loop: apply an outer multiplier update still pending.
 __global__ void flush_lambda_kernel(DevGrid G, DevOpts O)
 {

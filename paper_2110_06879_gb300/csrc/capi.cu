@@ -320,6 +320,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     size_t o_gb = cv.take<int32_t>(ng > 0 ? ng : 1);
     size_t o_gc = cv.take<double>(3 * (size_t)ng + 1), o_glim = cv.take<double>(4 * (size_t)ng + 1);
     size_t o_gu = cv.take<double>(2 * (size_t)ng + 1);
+    size_t o_gbase = cv.take<double>(2 * (size_t)ng + 1);
     size_t o_bus = cv.take<double>(6 * (size_t)nb), o_bw = cv.take<double>(nb), o_bth = cv.take<double>(nb);
     size_t o_rp = cv.take<int32_t>(nb + 1), o_col = cv.take<int32_t>(ns);
     size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
@@ -355,6 +356,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     G.raw = (double *)(base + o_raw);
     G.gen_bus = (int32_t *)(base + o_gb);
     G.gc = (double *)(base + o_gc); G.glim = (double *)(base + o_glim); G.gu = (double *)(base + o_gu);
+    G.gbase = (double *)(base + o_gbase);
     G.bus = (double *)(base + o_bus); G.bw = (double *)(base + o_bw); G.bth = (double *)(base + o_bth);
     G.row_ptr = (int32_t *)(base + o_rp); G.col = (int32_t *)(base + o_col);
     G.sx = (double *)(base + o_sx); G.sz = (double *)(base + o_sz);
@@ -397,6 +399,7 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
             cudaMemcpy((void *)G.raw, raw.data(), raw.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(G.gc, gc.data(), gc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(G.glim, glim.data(), glim.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(G.gbase, glim.data(), 2 * (size_t)ng * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy((void *)G.f_bus, g->f_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy((void *)G.t_bus, g->t_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
             (ng > 0 && cudaMemcpy((void *)G.gen_bus, g->gen_bus, ng * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
@@ -472,7 +475,17 @@ extern "C" int admm_set_gen_bounds(admm_handle *h, const double *pmin, const dou
     if (h->ng == 0) return ADMM_OK;
     CK(cudaMemcpyAsync(h->G.glim, pmin, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->G.glim + h->ng, pmax, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.gbase, h->G.glim, sizeof(double) * 2 * h->ng, cudaMemcpyDeviceToDevice, h->stream));
     return ADMM_OK;
+}
+
+extern "C" int admm_set_ramp_limit(admm_handle *h, double frac)
+{
+    if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
+    if (!(frac >= 0.0) || !std::isfinite(frac)) { set_err("ramp fraction must be >= 0"); return ADMM_ERR_INVALID_ARG; }
+    if (h->ng == 0) return ADMM_OK;
+    ramp_limit_kernel<<<(h->ng + 255) / 256, 256, 0, h->stream>>>(h->G, frac);
+    return launch_check("ramp_limit_kernel");
 }
 
 extern "C" int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, double tol,

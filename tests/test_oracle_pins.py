@@ -369,3 +369,20 @@ def test_tiny_admm_solves_acopf(oracle_mod):
     assert ref["success"]
     assert abs(sol["objective"] - ref["objective"]) <= 1e-4 * ref["objective"]
     assert sol["objective"] <= cost(grid.pg0, grid) * (1 + 1e-4)
+
+
+def test_ramp_limit_bounds(oracle_mod):
+    """Section IV-C ramp limit: bounds become [max(pmin, pg - r), min(pmax, pg + r)],
+    r = 0.02 pmax, around the current dispatch; a solve then keeps
+    |pg_new - pg_old| <= r."""
+    grid = synth.tiny_grid(3)
+    o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4)
+    o.solve(tol=0.0, max_iter=15)
+    pg0 = o.get(oracle_mod.U)[0:2 * grid.ngen:2].copy()
+    o.set_ramp_limit(0.02)
+    o.set_loads(grid.pd * 1.05, grid.qd * 1.05)
+    o.solve(tol=0.0, max_iter=10, warm_start=True)
+    pg1 = o.get(oracle_mod.U)[0:2 * grid.ngen:2]
+    r = 0.02 * grid.pmax
+    assert np.all(pg1 >= np.maximum(grid.pmin, pg0 - r) - 1e-15)
+    assert np.all(pg1 <= np.minimum(grid.pmax, pg0 + r) + 1e-15)
