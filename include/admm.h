@@ -4,8 +4,9 @@
  * "Accelerated Computation and Tracking of AC Optimal Power Flow Solutions
  * Using GPUs" (arXiv 2110.06879).
  *
- * One handle holds one grid resident on the current CUDA device.  Every
- * iteration of Algorithm 1 runs on the device:
+ * One handle holds one grid -- or a batch of independent grids ("scenarios",
+ * admm_create_batch) -- resident on the current CUDA device.  Every iteration
+ * of Algorithm 1 runs on the device, for all scenarios at once:
  *   branch_tron  -- eq. branch per branch (TRON inside an augmented Lagrangian on
  *                   the line limits, Section II-C / III-B), one thread per branch;
  *   bus_dual     -- eq. qp-bound for generators, eq. qp-bus per bus over a CSR
@@ -124,7 +125,26 @@ void admm_default_options(admm_options *o);
  * state on the current device and cold-start it (Section IV-B).
  * o == NULL selects the defaults.  On success *out owns the handle. */
 int admm_create(const admm_grid *g, const admm_options *o, admm_handle **out);
+
+/* A batch of nscen independent grids in one handle (grids[0..nscen-1], each
+ * validated like admm_create).  Their components are concatenated into one set
+ * of device arrays (a flattened component index); every iteration solves all
+ * branch subproblems of all running scenarios in one persistent launch and all
+ * bus rows in one launch, while each scenario keeps its own loop counters,
+ * penalties, tolerance and stopping decision (a per-scenario convergence mask).
+ * Bus blocks never straddle scenarios, so a scenario's reductions -- and thus
+ * its iterates -- are the same as when it is solved alone.  Per-scenario calls
+ * (set_loads*, set_gen_bounds, set_ramp_limit, get_solution, get_residuals,
+ * get_vector, get_csr) address the scenario chosen by admm_select_scenario
+ * (0 after creation).  admm_create is the batch of one. */
+int admm_create_batch(const admm_grid *grids, int32_t nscen, const admm_options *o,
+                      admm_handle **out);
 void admm_destroy(admm_handle *h);
+
+/* Number of scenarios of the handle (0 for NULL). */
+int32_t admm_scenario_count(admm_handle *h);
+/* Address scenario s (0 <= s < count) with the per-scenario calls. */
+int admm_select_scenario(admm_handle *h, int32_t s);
 
 /* Run all device work of this handle on the given cudaStream_t (NULL: the
  * legacy default stream).  The stream must outlive its use by the handle. */
@@ -161,9 +181,27 @@ int admm_set_ramp_limit(admm_handle *h, double frac);
 int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
                int32_t warm_start);
 /* Same, without waiting: the work is enqueued on the handle's stream; read the
- * outcome with admm_get_residuals after synchronising that stream. */
+ * outcome with admm_get_residuals after synchronising that stream.  With
+ * several scenarios both calls start every scenario with the same arguments;
+ * admm_solve returns ADMM_OK only when all of them converged (the most severe
+ * error otherwise). */
 int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
                      int32_t warm_start);
+
+/* Continuous batching.  admm_slot_begin (re)starts scenario s alone -- cold
+ * (warm_start = 0, Section IV-B) or from its resident state (1, Section IV-C)
+ * -- with its own penalties, tolerance and iteration cap; other scenarios keep
+ * running or idle.  admm_run enqueues at most max_iters iterations of the
+ * batched loop (one CUDA-graph launch) over the scenarios that are running;
+ * it returns early on the device once none is.  Both are asynchronous on the
+ * handle's stream; scenarios begun while a run is queued join the next run.
+ * admm_slot_status waits for the stream and writes, per scenario, 2 while it is
+ * still running or else its solve status (ADMM_OK, ADMM_NOT_CONVERGED, ...),
+ * and its iteration count; either pointer may be NULL. */
+int admm_slot_begin(admm_handle *h, int32_t s, double rho_pq, double rho_va, double tol,
+                    int32_t max_iter, int32_t warm_start);
+int admm_run(admm_handle *h, int32_t max_iters);
+int admm_slot_status(admm_handle *h, int32_t *status, int32_t *iters);
 
 /* Section IV-A solution: pg, qg [ngen] from the generator subproblems, vm, va
  * [nbus] from the bus subproblems (vm = sqrt(w)), branch flows pf, qf, pt, qt
@@ -173,8 +211,8 @@ int admm_get_solution(admm_handle *h, double *pg, double *qg, double *vm, double
                       double *qf, double *pt, double *qt);
 int admm_get_residuals(admm_handle *h, admm_residuals *out);
 
-/* Per-iteration residual history of the last solve: rows of 4 doubles
- * (primal, dual, z_norm, primal_z); returns the number of rows written
+/* Per-iteration residual history of scenario 0's last solve: rows of 4
+ * doubles (primal, dual, z_norm, primal_z); returns the number of rows written
  * (at most cap; the device keeps the last 65536 iterations). */
 int32_t admm_get_history(admm_handle *h, double *out, int32_t cap);
 
@@ -193,14 +231,15 @@ int admm_get_vector(admm_handle *h, int32_t which, double *out);
  * with entry 2l (+1) the from (to) end of branch l and 2 nbranch + g generator g. */
 int admm_get_csr(admm_handle *h, int32_t *row_ptr, int32_t *col);
 
-/* Counters of the last solve (summed over branches): TRON calls, TRON
+/* Counters of the last run (summed over all branches): TRON calls, TRON
  * iterations, gradient/Hessian evaluations, function evaluations, Cauchy
  * trials, CG iterations, projected-search trials, AL passes, TRON cap hits. */
 int admm_get_stats(admm_handle *h, int64_t *out9);
 
-/* Checkpoint: the full iteration state as an opaque host blob.  Call with
- * buf == NULL to get the size in *len.  admm_set_state accepts only a blob of
- * the same grid shape; a following warm solve continues the saved trajectory. */
+/* Checkpoint: the full iteration state of every scenario as an opaque host
+ * blob.  Call with buf == NULL to get the size in *len.  admm_set_state accepts
+ * only a blob of the same shape; a following warm solve continues the saved
+ * trajectory. */
 int admm_get_state(admm_handle *h, void *buf, size_t *len);
 int admm_set_state(admm_handle *h, const void *buf, size_t len);
 

@@ -66,6 +66,13 @@ def lib():
         sig = {
             "admm_default_options": (None, [C.POINTER(admm_options)]),
             "admm_create": (C.c_int, [C.POINTER(admm_grid), C.POINTER(admm_options), C.POINTER(vp)]),
+            "admm_create_batch": (C.c_int, [C.POINTER(admm_grid), i32, C.POINTER(admm_options),
+                                            C.POINTER(vp)]),
+            "admm_scenario_count": (i32, [vp]),
+            "admm_select_scenario": (C.c_int, [vp, i32]),
+            "admm_slot_begin": (C.c_int, [vp, i32, d, d, d, i32, i32]),
+            "admm_run": (C.c_int, [vp, i32]),
+            "admm_slot_status": (C.c_int, [vp, vp, vp]),
             "admm_destroy": (None, [vp]),
             "admm_set_stream": (C.c_int, [vp, vp]),
             "admm_set_loads": (C.c_int, [vp, vp, vp]),
@@ -121,30 +128,63 @@ def default_options(**kw) -> admm_options:
     return o
 
 
+def _grid_struct(grid, keep: list) -> admm_grid:
+    g = admm_grid()
+    g.nbus, g.nbranch, g.ngen, g.ref_bus = grid.nbus, grid.nbranch, grid.ngen, grid.ref_bus
+    g.base_mva = grid.base_mva
+    for name in ("pd", "qd", "gs", "bs", "vmin", "vmax", "r", "x", "b", "tap", "shift",
+                 "rate_a", "pmin", "pmax", "qmin", "qmax", "c2", "c1", "c0"):
+        a = np.ascontiguousarray(getattr(grid, name), dtype=np.float64)
+        keep.append(a)
+        setattr(g, name, a.ctypes.data)
+    for name in ("f_bus", "t_bus", "gen_bus"):
+        a = np.ascontiguousarray(getattr(grid, name), dtype=np.int32)
+        keep.append(a)
+        setattr(g, name, a.ctypes.data)
+    return g
+
+
 class Solver:
-    """One grid resident on the current CUDA device (``admm_create``)."""
+    """One grid, or a batch of grids, resident on the current CUDA device
+    (``admm_create`` / ``admm_create_batch``).  Per-scenario methods address the
+    scenario chosen with ``select``."""
 
     def __init__(self, grid, stream=None, **opts):
-        self.grid = grid
-        self.nb, self.nl, self.ng = grid.nbus, grid.nbranch, grid.ngen
-        self.m = 2 * self.ng + 8 * self.nl
+        grids = list(grid) if isinstance(grid, (list, tuple)) else [grid]
+        self.grids = grids
         self.opts = default_options(**opts)
-        keep = {}
-        g = admm_grid()
-        g.nbus, g.nbranch, g.ngen, g.ref_bus = grid.nbus, grid.nbranch, grid.ngen, grid.ref_bus
-        g.base_mva = grid.base_mva
-        for name in ("pd", "qd", "gs", "bs", "vmin", "vmax", "r", "x", "b", "tap", "shift",
-                     "rate_a", "pmin", "pmax", "qmin", "qmax", "c2", "c1", "c0"):
-            keep[name] = np.ascontiguousarray(getattr(grid, name), dtype=np.float64)
-            setattr(g, name, keep[name].ctypes.data)
-        for name in ("f_bus", "t_bus", "gen_bus"):
-            keep[name] = np.ascontiguousarray(getattr(grid, name), dtype=np.int32)
-            setattr(g, name, keep[name].ctypes.data)
+        keep = []
+        arr = (admm_grid * len(grids))(*[_grid_struct(g, keep) for g in grids])
         h = C.c_void_p()
-        _check(lib().admm_create(C.byref(g), C.byref(self.opts), C.byref(h)), "admm_create")
+        _check(lib().admm_create_batch(arr, len(grids), C.byref(self.opts), C.byref(h)),
+               "admm_create_batch")
         self.h = h
+        self.nscen = len(grids)
+        self.select(0)
         if stream is not None:
             self.set_stream(stream)
+
+    def select(self, s: int):
+        _check(lib().admm_select_scenario(self.h, s), "admm_select_scenario")
+        g = self.grids[s]
+        self.grid = g
+        self.nb, self.nl, self.ng = g.nbus, g.nbranch, g.ngen
+        self.m = 2 * self.ng + 8 * self.nl
+
+    def slot_begin(self, s, tol=1e-4, max_iter=5000, warm_start=False, rho_pq=None, rho_va=None):
+        rp = self.opts.rho_pq if rho_pq is None else rho_pq
+        rv = self.opts.rho_va if rho_va is None else rho_va
+        _check(lib().admm_slot_begin(self.h, s, rp, rv, tol, max_iter, 1 if warm_start else 0),
+               "admm_slot_begin")
+
+    def run(self, max_iters):
+        _check(lib().admm_run(self.h, max_iters), "admm_run")
+
+    def slot_status(self):
+        st = np.zeros(self.nscen, dtype=np.int32)
+        it = np.zeros(self.nscen, dtype=np.int32)
+        _check(lib().admm_slot_status(self.h, _ptr(st), _ptr(it)), "admm_slot_status")
+        return st, it
 
     def close(self):
         if getattr(self, "h", None):

@@ -30,19 +30,24 @@ enum StatId { ST_TRON_CALLS = 0, ST_TRON_ITERS, ST_FGH, ST_F, ST_CAUCHY, ST_CG, 
 // Loop status kept on the device.
 enum { CS_RUNNING = 2 };
 
-struct Ctrl {
-    // per-solve inputs (written by the begin kernel)
+// Per-scenario state of Algorithm 1.  A handle holds S scenarios (independent
+// grids) concatenated into one set of arrays; each scenario runs its own loop
+// counters, penalties, tolerances and stopping decision.
+struct SCtrl {
     double tol, rho_pq, rho_va;
-    int32_t max_iter, warm;
-    // loop state (Algorithm 1)
-    int32_t iter, inner, outer, status, done, pending, total_iters, pad0;
     double beta, beta_used, tol_in, zprev;
-    double pri, dual, zn, pri_z;
-    double eps_pri, eps_dual;
-    // finalize outputs
+    double pri, dual, zn, pri_z, eps_pri, eps_dual;
     double objective, max_viol;
-    unsigned int counter;          // last-block detection of bus_dual
-    unsigned int fin_counter;      // last-block detection of finalize
+    int32_t max_iter, iter, inner, outer, status, done, pending, active;
+    int32_t total_iters, ref, m, pad;
+    unsigned int counter;          // last-block ticket of bus_dual for this scenario
+    unsigned int fin_counter;      // last-block ticket of finalize for this scenario
+};
+
+// Whole-handle state of one run of the iteration loop.
+struct Ctrl {
+    int32_t run_iter, run_max, n_live, done;
+    int32_t total_iters, pad0;
     unsigned int branch_next;      // work queue head of branch_tron (reset every iteration)
     unsigned int pad1;
     // longest-first scheduling of branch_tron: branches filed by the loop trips
@@ -60,10 +65,16 @@ struct DevOpts {
 };
 
 struct DevGrid {
-    int32_t nb, nl, ng, ns, ref;
-    int32_t nblk_bus;              // blocks of the bus_dual launch
+    int32_t nb, nl, ng, ns, S;
+    int32_t nblk_bus;              // blocks of the bus_dual launch (aligned per scenario)
     int32_t nblk_branch;           // blocks of the (persistent) branch_tron launch
     int32_t pad_;
+    // scenario layout: index ranges [off[s], off[s+1]) of each scenario
+    const int32_t *bus_off, *br_off, *gen_off, *slot_off, *blk_off;
+    const int32_t *blk_scen;       // [nblk_bus] scenario of each bus block
+    const int32_t *br_scen;        // [nl] scenario of each branch
+    const int32_t *slot_scen;      // [ns] scenario of each incidence slot
+    SCtrl *sc;                     // [S]
     // branches
     const int32_t *f_bus, *t_bus;
     double *Y, *lim, *bx, *blt, *bt, *bu;
@@ -80,8 +91,8 @@ struct DevGrid {
     // scratch and control
     int32_t *cls_list;             // [2][3][nl] branch ids per (parity, class)
     double *partials;              // [nblk_bus][8]
-    double *fin_partials;          // [nblk_fin][2]
-    double *hist;                  // [kHistCap][4]
+    double *fin_partials;          // [nblk_fin][2] (one scenario at a time)
+    double *hist;                  // [kHistCap][4], scenario 0 only
     Ctrl *ctrl;
     double line_limit_frac;
 };
@@ -91,17 +102,25 @@ struct SolveParams {
     int32_t max_iter, warm;
 };
 
+// index ranges of one scenario, for the kernels that work on one scenario
+struct Range {
+    int32_t s, b0, b1, k0, k1, i0, i1, g0, g1;
+};
+
 // kernels
 __global__ void admittance_kernel(DevGrid G);
-__global__ void cold_start_kernel(DevGrid G, double beta_init);
-__global__ void begin_kernel(DevGrid G, DevOpts O, SolveParams P);
+__global__ void cold_start_kernel(DevGrid G, Range R, double beta_init);
+__global__ void slot_begin_kernel(DevGrid G, DevOpts O, int32_t s0, int32_t s1, SolveParams P);
+__global__ void run_begin_kernel(DevGrid G, int32_t run_max);
 __global__ void branch_tron_kernel(DevGrid G, DevOpts O);
-__global__ void bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond,
-                                int32_t use_cond);
+__global__ void bus_dual_kernel(DevGrid G, DevOpts O);
+__global__ void control_kernel(DevGrid G, cudaGraphConditionalHandle cond, int32_t use_cond);
 __global__ void flush_lambda_kernel(DevGrid G, DevOpts O);
-__global__ void ramp_limit_kernel(DevGrid G, double frac);
-__global__ void finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va,
-                                double *pf, double *qf, double *pt, double *qt, int32_t nblk);
+__global__ void clear_pending_kernel(DevGrid G);
+__global__ void ramp_limit_kernel(DevGrid G, Range R, double frac);
+__global__ void finalize_kernel(DevGrid G, Range R, double *pg, double *qg, double *vm,
+                                double *va, double *pf, double *qf, double *pt, double *qt,
+                                int32_t nblk);
 
 constexpr int kBranchBlock = 128;
 constexpr int kBranchBlocksPerSM = 1;

@@ -556,6 +556,25 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long *dst, int v)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
+// File the branches some lanes finished (filed >= 0) into the class lists of
+// the next iteration (warp-collective; one atomic per class and warp).
+__device__ __forceinline__ void file_branches(Ctrl *ctrl, int32_t *lnxt, int nl, int nxt, int lane,
+                                              int filed, int fcls)
+{
+#pragma unroll
+    for (int cl = 0; cl < 3; ++cl) {
+        const unsigned m = __ballot_sync(kFull, filed >= 0 && fcls == cl);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&ctrl->cls_count[nxt][cl], (unsigned)__popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (filed >= 0 && fcls == cl)
+                lnxt[(size_t)cl * nl + base + __popc(m & ((1u << lane) - 1u))] = filed;
+        }
+    }
+}
+
 enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE = 4 };
 
 }  // namespace
@@ -570,8 +589,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     const int lane = threadIdx.x & 31;
     const double *sY = sh + threadIdx.x;
     const double *sT = sh + 8 * kBranchBlock + threadIdx.x;
-    const double rpq = ctrl->rho_pq, rva = ctrl->rho_va;
-    const double rt0 = O.al_rho0 > 0.0 ? O.al_rho0 : rpq;
+    double rpq = 1.0, rva = 1.0, rt0 = 1.0;   // penalties of the lane's branch's scenario
     Cnt c = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     // queue order: the classes filed by the previous iteration, hardest first
@@ -665,60 +683,63 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 state = LS_INIT;
             }
         }
-        // (F) file finished branches by the work they took (one atomic per class and warp)
-#pragma unroll
-        for (int cl = 0; cl < 3; ++cl) {
-            const unsigned m = __ballot_sync(kFull, filed >= 0 && fcls == cl);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(&ctrl->cls_count[nxt][cl], (unsigned)__popc(m));
-                base = __shfl_sync(kFull, base, leader);
-                if (filed >= 0 && fcls == cl)
-                    lnxt[(size_t)cl * nl + base + __popc(m & ((1u << lane) - 1u))] = filed;
-            }
-        }
-        // (R) refill idle lanes from the branch queue (one atomic per warp)
-        const unsigned need = __ballot_sync(kFull, state == LS_IDLE && !exhausted);
-        if (need) {
+        // (F) file finished branches by the work they took
+        file_branches(ctrl, lnxt, nl, nxt, lane, filed, fcls);
+        // (R) refill idle lanes from the branch queue (one atomic per warp);
+        // branches of scenarios that are not iterating are filed and skipped
+        for (int rep = 0; rep < 64; ++rep) {
+            const unsigned need = __ballot_sync(kFull, state == LS_IDLE && !exhausted);
+            if (!need) break;
             const int leader = __ffs(need) - 1;
             unsigned base = 0;
             if (lane == leader) base = atomicAdd(&ctrl->branch_next, (unsigned)__popc(need));
             base = __shfl_sync(kFull, base, leader);
+            int skip = -1;
             if (state == LS_IDLE && !exhausted) {
                 const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
                 if (idx < (unsigned)nl) {
-                    b = !ordered ? (int)idx
+                    const int bb = !ordered ? (int)idx
                         : idx < n0 ? lcur[idx]
                         : idx < n0 + n1 ? lcur[nl + (idx - n0)]
                                         : lcur[2 * (size_t)nl + (idx - n0 - n1)];
-                    trips = 0;
-                    double *my = sh + threadIdx.x;
+                    const SCtrl *sc = G.sc + G.br_scen[bb];
+                    if (!sc->active || sc->done) {
+                        skip = bb;
+                    } else {
+                        b = bb;
+                        rpq = sc->rho_pq;
+                        rva = sc->rho_va;
+                        rt0 = O.al_rho0 > 0.0 ? O.al_rho0 : rpq;
+                        trips = 0;
+                        double *my = sh + threadIdx.x;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        my[i * kBranchBlock] = G.Y[i * nl + b];
-                        my[(8 + i) * kBranchBlock] = G.bt[i * nl + b];
+                        for (int i = 0; i < 8; ++i) {
+                            my[i * kBranchBlock] = G.Y[i * nl + b];
+                            my[(8 + i) * kBranchBlock] = G.bt[i * nl + b];
+                        }
+                        B.vlo_i = G.lim[0 * nl + b];
+                        B.vhi_i = G.lim[1 * nl + b];
+                        B.vlo_j = G.lim[2 * nl + b];
+                        B.vhi_j = G.lim[3 * nl + b];
+                        B.slo = G.lim[4 * nl + b];
+                        B.set_keys();
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
+                        lt0 = G.blt[b];
+                        lt1 = G.blt[nl + b];
+                        rt = rt0;
+                        hprev = __longlong_as_double(0x7ff0000000000000LL);
+                        apass = 0;
+                        state = LS_INIT;
                     }
-                    B.vlo_i = G.lim[0 * nl + b];
-                    B.vhi_i = G.lim[1 * nl + b];
-                    B.vlo_j = G.lim[2 * nl + b];
-                    B.vhi_j = G.lim[3 * nl + b];
-                    B.slo = G.lim[4 * nl + b];
-                    B.set_keys();
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
-                    lt0 = G.blt[b];
-                    lt1 = G.blt[nl + b];
-                    rt = rt0;
-                    hprev = __longlong_as_double(0x7ff0000000000000LL);
-                    apass = 0;
-                    state = LS_INIT;
                 } else {
                     exhausted = true;
                 }
             }
+            file_branches(ctrl, lnxt, nl, nxt, lane, skip, 2);
         }
-        if (!__any_sync(kFull, state != LS_IDLE)) break;
+        // done when every lane is idle and the queue is drained
+        if (!__any_sync(kFull, state != LS_IDLE || !exhausted)) break;
         // (I) a TRON solve starts from the current point; a rejected step gets
         // its gradient and Hessian back at the kept point
         if (state == LS_INIT) {

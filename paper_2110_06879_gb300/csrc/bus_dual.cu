@@ -9,9 +9,13 @@
 // the same thread before the bus update.  The outer multiplier update
 // lambda <- Proj(lambda + beta z) is applied lazily: lambda is read only by the
 // z update, so the bus row applies a pending outer update to its slots just
-// before it updates z.  Each block writes four partial sums; the last block to
-// finish (atomic ticket) sums them in block order, evaluates the stopping
-// tests and the outer step, and sets the CUDA-graph conditional.
+// before it updates z.  Bus blocks never straddle scenarios (each scenario's
+// buses start on a block boundary), so every block writes its partial sums for
+// exactly one scenario; the scenario's last block to finish (atomic ticket)
+// sums them in block order, evaluates that scenario's stopping tests and outer
+// step.  A scenario's result is therefore the same whether it is solved alone
+// or batched with others.  control_kernel ends each iteration: it sets the
+// CUDA-graph conditional while any scenario is still running.
 #include "admm_internal.cuh"
 
 namespace admm {
@@ -100,15 +104,17 @@ __global__ void admittance_kernel(DevGrid G)
     G.lim[4 * nl + l] = rate > 0.0 ? -rb * rb : -1e20;
 }
 
-// Section IV-B initialisation (cold start).  Thread roles: [0, nl) branches,
-// [nl, nl + ns) slots, [nl + ns, nl + ns + nb) buses, then generators.
-__global__ void cold_start_kernel(DevGrid G, double beta_init)
+// Section IV-B initialisation (cold start) of one scenario.  Thread roles:
+// its branches, its incidence slots, its buses, its generators, and one more
+// thread for the scenario's outer state.
+__global__ void cold_start_kernel(DevGrid G, Range R, double beta_init)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nl = G.nl, nb = G.nb, ng = G.ng, ns = G.ns;
     const double *vmin = G.bus + 4 * nb, *vmax = G.bus + 5 * nb;
-    if (t < nl) {
-        int l = t, i = G.f_bus[l], j = G.t_bus[l];
+    const int nbr = R.b1 - R.b0, nsl = R.k1 - R.k0, nbu = R.i1 - R.i0, nge = R.g1 - R.g0;
+    if (t < nbr) {
+        const int l = R.b0 + t, i = G.f_bus[l], j = G.t_bus[l];
         double vi = 0.5 * (vmin[i] + vmax[i]), vj = 0.5 * (vmin[j] + vmax[j]);
         double fl[4];
         flows_at(G.Y, nl, l, vi, vj, 0.0, fl);
@@ -125,9 +131,10 @@ __global__ void cold_start_kernel(DevGrid G, double beta_init)
         }
         return;
     }
-    int k = t - nl;
-    if (k < ns) {
-        int e = G.col[k];
+    int q = t - nbr;
+    if (q < nsl) {
+        const int k = R.k0 + q;
+        const int e = G.col[k];
         double cp, cq;
         if (e < 2 * nl) {
             int l = e >> 1, end = e & 1, i = G.f_bus[l], j = G.t_bus[l];
@@ -150,71 +157,86 @@ __global__ void cold_start_kernel(DevGrid G, double beta_init)
         }
         return;
     }
-    int i = k - ns;
-    if (i < nb) {
+    q -= nsl;
+    if (q < nbu) {
+        const int i = R.i0 + q;
         double v = 0.5 * (vmin[i] + vmax[i]);
         G.bw[i] = v * v;
         G.bth[i] = 0.0;
         return;
     }
-    int g = i - nb;
-    if (g < ng) {
+    q -= nbu;
+    if (q < nge) {
+        const int g = R.g0 + q;
         G.gu[g] = 0.5 * (G.glim[0 * ng + g] + G.glim[1 * ng + g]);
         G.gu[ng + g] = 0.5 * (G.glim[2 * ng + g] + G.glim[3 * ng + g]);
+        return;
     }
-    if (g == ng) {   // one thread past the generators resets the outer state
-        Ctrl *c = G.ctrl;
+    if (q == nge) {   // the scenario's outer state
+        SCtrl *c = G.sc + R.s;
         c->beta = beta_init;
         c->pending = 0;
         c->total_iters = 0;
-        for (int q = 0; q < 2; ++q)
-            for (int r = 0; r < 4; ++r) c->cls_count[q][r] = 0u;
     }
 }
 
-// Per-solve reset of the loop counters (Algorithm 1 restarts its loops; the
-// primal, dual and penalty values stay).
-__global__ void begin_kernel(DevGrid G, DevOpts O, SolveParams P)
+// Start (or restart) the loops of scenarios [s0, s1): Algorithm 1 restarts its
+// counters; the primal, dual and penalty values stay (warm start).
+__global__ void slot_begin_kernel(DevGrid G, DevOpts O, int32_t s0, int32_t s1, SolveParams P)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    Ctrl *c = G.ctrl;
+    const int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= s1) return;
+    SCtrl *c = G.sc + s;
     c->tol = P.tol;
     c->rho_pq = P.rho_pq;
     c->rho_va = P.rho_va;
     c->max_iter = P.max_iter;
-    c->warm = P.warm;
     c->iter = 0;
     c->inner = 0;
     c->outer = 0;
     c->status = CS_RUNNING;
     c->done = P.max_iter <= 0 ? 1 : 0;
+    c->active = 1;
     c->zprev = __longlong_as_double(0x7ff0000000000000LL);
     c->tol_in = fmax(O.tol_in0, P.tol);
     c->counter = 0;
+}
+
+// Start one run of the iteration loop over every active scenario.
+__global__ void run_begin_kernel(DevGrid G, int32_t run_max)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctrl *c = G.ctrl;
+    int live = 0;
+    for (int s = 0; s < G.S; ++s) live += (G.sc[s].active && !G.sc[s].done) ? 1 : 0;
+    c->run_iter = 0;
+    c->run_max = run_max;
+    c->n_live = live;
+    c->done = (live == 0 || run_max <= 0) ? 1 : 0;
     c->branch_next = 0;
     for (int k = 0; k < kNumStats; ++k) c->stats[k] = 0;
 }
 
 __global__ void __launch_bounds__(kBusBlock)
-bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t use_cond)
+bus_dual_kernel(DevGrid G, DevOpts O)
 {
     __shared__ double sh[kBusBlock / 32][7];
     __shared__ bool last;
-    Ctrl *ctrl = G.ctrl;
-    if (ctrl->done) {
-        // the loop is over: keep the graph's WHILE condition at 0
-        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
-        return;
-    }
+    if (G.ctrl->done) return;
+    const int sid = G.blk_scen[blockIdx.x];
+    SCtrl *c = G.sc + sid;
+    if (!c->active || c->done) return;      // this scenario is not iterating
     const int nb = G.nb, nl = G.nl, ng = G.ng, ns = G.ns;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const double rpq = ctrl->rho_pq, rva = ctrl->rho_va, beta = ctrl->beta;
-    const bool pending = ctrl->pending != 0;
-    const double bused = ctrl->beta_used, lmax = O.lambda_max;
+    const int blk0 = G.blk_off[sid], nblk_s = G.blk_off[sid + 1] - blk0;
+    const int i = G.bus_off[sid] + (blockIdx.x - blk0) * blockDim.x + threadIdx.x;
+    const int i_end = G.bus_off[sid + 1];
+    const double rpq = c->rho_pq, rva = c->rho_va, beta = c->beta;
+    const bool pending = c->pending != 0;
+    const double bused = c->beta_used, lmax = O.lambda_max;
     const bool two = O.two_level != 0;
     // |u-xbar|^2, |u-xbar+z|^2, |rho dxbar|^2, |z|^2, |u|^2, |xbar|^2, |y|^2
     double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (i < nb) {
+    if (i < i_end) {
         const int r0 = G.row_ptr[i], r1 = G.row_ptr[i + 1];
         const double so = O.obj_scale;
         // pass 1: generator updates, then the bus QP sums
@@ -266,7 +288,7 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
         const double mu0 = (M11 * rP - M01 * rQ) / det;
         const double mu1 = (M00 * rQ - M01 * rP) / det;
         const double w = (cw + gs * mu0 - bs * mu1) / qw;
-        const double th = (i == G.ref) ? 0.0 : ct / qt;
+        const double th = (i == c->ref) ? 0.0 : ct / qt;
         const double dw = w - G.bw[i], dth = th - G.bth[i];
         G.bw[i] = w;
         G.bth[i] = th;
@@ -334,42 +356,36 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
         double *pp = G.partials + 8 * blockIdx.x;
         for (int k = 0; k < 7; ++k) pp[k] = acc[k];
         __threadfence();
-        unsigned int ticket = atomicAdd(&ctrl->counter, 1u);
-        last = ticket == gridDim.x - 1;
+        unsigned int ticket = atomicAdd(&c->counter, 1u);
+        last = ticket == (unsigned)nblk_s - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // last block: fixed-order sum of the block partials
+    // the scenario's last block: fixed-order sum of its block partials
     double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        const volatile double *pp = G.partials + 8 * b;
+    for (int b = threadIdx.x; b < nblk_s; b += blockDim.x) {
+        const volatile double *pp = G.partials + 8 * (blk0 + b);
         for (int k = 0; k < 7; ++k) v[k] += pp[k];
     }
     block_sum<kBusBlock, 7>(v, sh);
     if (threadIdx.x != 0) return;
-    Ctrl *c = ctrl;
     c->counter = 0;
-    c->branch_next = 0;     // the next branch_tron launch starts its queue at 0
     const double pri = sqrt(v[0]), pri_z = sqrt(v[1]), dual = sqrt(v[2]), zn = sqrt(v[3]);
     c->pri = pri; c->pri_z = pri_z; c->dual = dual; c->zn = zn;
     // standard ADMM tolerances (absolute and relative both t):
     // eps_pri(t) = sqrt(m) t + t max(|u|, |xbar|), eps_dual(t) = sqrt(m) t + t |y|
-    const double sqm = sqrt((double)(2 * ng + 8 * nl));
+    const double sqm = sqrt((double)c->m);
     const double nux = fmax(sqrt(v[4]), sqrt(v[5])), ny = sqrt(v[6]);
     const double ep = sqm * c->tol + c->tol * nux, ed = sqm * c->tol + c->tol * ny;
     c->eps_pri = ep;
     c->eps_dual = ed;
-    double *h = G.hist + 4 * (c->iter % kHistCap);
-    h[0] = pri; h[1] = dual; h[2] = zn; h[3] = pri_z;
+    if (sid == 0) {
+        double *h = G.hist + 4 * (c->iter % kHistCap);
+        h[0] = pri; h[1] = dual; h[2] = zn; h[3] = pri_z;
+    }
     c->iter += 1;
     c->total_iters += 1;
-    // the branch lists filled by this iteration become the next queue order;
-    // the ones it consumed are emptied to be filled next
-    {
-        const int nxt = (c->total_iters + 1) & 1;
-        for (int r = 0; r < 4; ++r) c->cls_count[nxt][r] = 0u;
-    }
     int stop = 0;
     c->pending = 0;
     if (!isfinite(pri) || !isfinite(dual) || !isfinite(zn)) {
@@ -404,18 +420,41 @@ bus_dual_kernel(DevGrid G, DevOpts O, cudaGraphConditionalHandle cond, int32_t u
             stop = 1;
         }
     }
-    c->done = stop;
+    if (stop) {
+        c->done = 1;
+        atomicSub(&G.ctrl->n_live, 1);
+    }
+}
+
+// End of one iteration: the next branch_tron queue, the scheduling classes,
+// and whether the loop goes on (some scenario still running, run cap not hit).
+__global__ void control_kernel(DevGrid G, cudaGraphConditionalHandle cond, int32_t use_cond)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Ctrl *c = G.ctrl;
+    int stop = c->done;
+    if (!stop) {
+        c->run_iter += 1;
+        c->total_iters += 1;
+        c->branch_next = 0;
+        // the branch lists filled by this iteration become the next queue order;
+        // the ones it consumed are emptied to be filled next
+        const int nxt = (c->total_iters + 1) & 1;
+        for (int r = 0; r < 4; ++r) c->cls_count[nxt][r] = 0u;
+        stop = (c->n_live <= 0 || c->run_iter >= c->run_max) ? 1 : 0;
+        c->done = stop;
+    }
     if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
 // Ramp limit of Section IV-C around the current dispatch pg:
 // pmin' = max(pmin, pg - frac pmax), pmax' = min(pmax, pg + frac pmax) on the
 // bounds last set by the caller (pmin' kept <= pmax').
-__global__ void ramp_limit_kernel(DevGrid G, double frac)
+__global__ void ramp_limit_kernel(DevGrid G, Range R, double frac)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = R.g0 + blockIdx.x * blockDim.x + threadIdx.x;
     const int ng = G.ng;
-    if (g >= ng) return;
+    if (g >= R.g1) return;
     const double lo = G.gbase[g], hi = G.gbase[ng + g], pg = G.gu[g];
     const double r = frac * hi;
     const double nhi = fmin(hi, pg + r);
@@ -426,12 +465,18 @@ __global__ void ramp_limit_kernel(DevGrid G, double frac)
 // After the loop: apply an outer multiplier update still pending.
 __global__ void flush_lambda_kernel(DevGrid G, DevOpts O)
 {
-    Ctrl *ctrl = G.ctrl;
-    if (!ctrl->pending) return;
     const int ns = G.ns;
-    const double bused = ctrl->beta_used, lmax = O.lambda_max;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * ns; t += gridDim.x * blockDim.x)
-        G.sl[t] = clampd(G.sl[t] + bused * G.sz[t], -lmax, lmax);
+    const double lmax = O.lambda_max;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * ns; t += gridDim.x * blockDim.x) {
+        const SCtrl *c = G.sc + G.slot_scen[t % ns];
+        if (c->pending) G.sl[t] = clampd(G.sl[t] + c->beta_used * G.sz[t], -lmax, lmax);
+    }
+}
+
+__global__ void clear_pending_kernel(DevGrid G)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < G.S) G.sc[s].pending = 0;
 }
 
 // Section IV-A solution extraction and ||c(x)||_inf.  Roles: [0, nb) buses
@@ -439,19 +484,21 @@ __global__ void flush_lambda_kernel(DevGrid G, DevOpts O)
 // branches (flows from bus voltages, line limits), [nb + nl, ...) generators
 // (cost).  The last block reduces the per-block max violation and cost.
 __global__ void __launch_bounds__(kFinBlock)
-finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va, double *pf,
+finalize_kernel(DevGrid G, Range R, double *pg, double *qg, double *vm, double *va, double *pf,
                 double *qf, double *pt, double *qt, int32_t nblk)
 {
     __shared__ double sh[kFinBlock / 32][2];
     __shared__ bool last;
     const int nb = G.nb, nl = G.nl, ng = G.ng;
+    const int nbs = R.i1 - R.i0, nls = R.b1 - R.b0, ngs = R.g1 - R.g0;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     double viol = 0.0, obj = 0.0;
-    if (t < nb) {
-        const int i = t;
+    // outputs are indexed locally within the scenario
+    if (t < nbs) {
+        const int i = R.i0 + t;
         const double v = sqrt(fmax(G.bw[i], 0.0));
-        if (vm) vm[i] = v;
-        if (va) va[i] = G.bth[i];
+        if (vm) vm[t] = v;
+        if (va) va[t] = G.bth[i];
         const double w2 = v * v;
         double bp = -G.bus[i] - G.bus[2 * nb + i] * w2;
         double bq = -G.bus[nb + i] + G.bus[3 * nb + i] * w2;
@@ -470,23 +517,23 @@ finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va, doubl
             }
         }
         viol = fmax(fmax(fabs(bp), fabs(bq)), fmax(v - G.bus[5 * nb + i], G.bus[4 * nb + i] - v));
-    } else if (t < nb + nl) {
-        const int l = t - nb, fi = G.f_bus[l], tj = G.t_bus[l];
+    } else if (t < nbs + nls) {
+        const int l = R.b0 + t - nbs, lo = t - nbs, fi = G.f_bus[l], tj = G.t_bus[l];
         double fl[4];
         flows_at(G.Y, nl, l, sqrt(fmax(G.bw[fi], 0.0)), sqrt(fmax(G.bw[tj], 0.0)),
                  G.bth[fi] - G.bth[tj], fl);
-        if (pf) pf[l] = fl[0];
-        if (qf) qf[l] = fl[1];
-        if (pt) pt[l] = fl[2];
-        if (qt) qt[l] = fl[3];
+        if (pf) pf[lo] = fl[0];
+        if (qf) qf[lo] = fl[1];
+        if (pt) pt[lo] = fl[2];
+        if (qt) qt[lo] = fl[3];
         const double rate = G.raw[5 * nl + l];
         if (rate > 0.0)
             viol = fmax(sqrt(fl[0] * fl[0] + fl[1] * fl[1]), sqrt(fl[2] * fl[2] + fl[3] * fl[3])) - rate;
-    } else if (t < nb + nl + ng) {
-        const int g = t - nb - nl;
+    } else if (t < nbs + nls + ngs) {
+        const int go = t - nbs - nls, g = R.g0 + go;
         const double P = G.gu[g];
-        if (pg) pg[g] = P;
-        if (qg) qg[g] = G.gu[ng + g];
+        if (pg) pg[go] = P;
+        if (qg) qg[go] = G.gu[ng + g];
         obj = G.gc[g] * P * P + G.gc[ng + g] * P + G.gc[2 * ng + g];
     }
     // block max of viol, block sum of obj
@@ -504,7 +551,7 @@ finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va, doubl
         G.fin_partials[2 * blockIdx.x] = mv;
         G.fin_partials[2 * blockIdx.x + 1] = so;
         __threadfence();
-        unsigned int ticket = atomicAdd(&G.ctrl->fin_counter, 1u);
+        unsigned int ticket = atomicAdd(&G.sc[R.s].fin_counter, 1u);
         last = ticket == (unsigned)nblk - 1;
     }
     __syncthreads();
@@ -516,9 +563,9 @@ finalize_kernel(DevGrid G, double *pg, double *qg, double *vm, double *va, doubl
         mv = fmax(mv, pp[0]);
         so += pp[1];
     }
-    G.ctrl->max_viol = mv;
-    G.ctrl->objective = so;
-    G.ctrl->fin_counter = 0;
+    G.sc[R.s].max_viol = mv;
+    G.sc[R.s].objective = so;
+    G.sc[R.s].fin_counter = 0;
 }
 
 }  // namespace admm

@@ -45,8 +45,8 @@ constexpr uint64_t kStateMagic = 0x41444d4d53543031ull;   // "ADMMST01"
 }  // namespace
 
 struct admm_handle {
-    int32_t nb = 0, nl = 0, ng = 0, ns = 0, ref = 0;
-    double base = 100.0;
+    int32_t S = 0;                        // scenarios
+    int32_t nb = 0, nl = 0, ng = 0, ns = 0;   // totals over scenarios
     admm_options opts{};
     DevGrid G{};
     DevOpts O{};
@@ -54,18 +54,21 @@ struct admm_handle {
     void *dmem = nullptr;        // one device allocation, carved into the arrays
     size_t dbytes = 0;
     double *dout = nullptr;      // finalize outputs [2 nb + 4 nl + 2 ng]
-    Ctrl *hctrl = nullptr;       // pinned host mirror of the device control block
+    Ctrl *hctrl = nullptr;       // pinned host mirror of the control block
+    SCtrl *hsc = nullptr;        // pinned host mirror of the scenario control blocks
+    // host copies of the layout (global indices)
     std::vector<int32_t> row_ptr, col, f_bus, t_bus, gen_bus;
-    int nblk_branch = 0, nblk_bus = 0, nblk_cold = 0, nblk_fin = 0, nblk_flush = 0;
+    std::vector<int32_t> bus_off, br_off, gen_off, slot_off, blk_off;
+    std::vector<double> base_mva;
+    int32_t sel = 0;             // scenario addressed by the per-scenario calls
+    int nblk_branch = 0, nblk_bus = 0, nblk_fin = 0, nblk_flush = 0;
     // iteration graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t begin_node = nullptr;
-    SolveParams begin_params{};
-    void *begin_args[3] = {nullptr, nullptr, nullptr};
+    int32_t begin_run_max = 0;
+    void *begin_args[2] = {nullptr, nullptr};
     bool graph_ok = false;
-    int last_status = ADMM_OK;
-    double last_obj = 0.0, last_viol = 0.0;
 };
 
 extern "C" void admm_default_options(admm_options *o)
@@ -197,22 +200,31 @@ int launch_check(const char *what)
     return ADMM_OK;
 }
 
+Range range_of(const admm_handle *h, int s)
+{
+    Range R;
+    R.s = s;
+    R.b0 = h->br_off[s]; R.b1 = h->br_off[s + 1];
+    R.k0 = h->slot_off[s]; R.k1 = h->slot_off[s + 1];
+    R.i0 = h->bus_off[s]; R.i1 = h->bus_off[s + 1];
+    R.g0 = h->gen_off[s]; R.g1 = h->gen_off[s + 1];
+    return R;
+}
+
+// run_begin -> WHILE { branch_tron -> bus_dual -> control } -> flush -> clear
 int build_graph(admm_handle *h)
 {
     cudaGraph_t graph;
     CK(cudaGraphCreate(&graph, 0));
     h->graph = graph;
-    // begin node (per-solve parameters are updated in the executable graph)
     h->begin_args[0] = &h->G;
-    h->begin_args[1] = &h->O;
-    h->begin_args[2] = &h->begin_params;
+    h->begin_args[1] = &h->begin_run_max;
     cudaKernelNodeParams kp{};
-    kp.func = (void *)begin_kernel;
+    kp.func = (void *)run_begin_kernel;
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(32);
     kp.kernelParams = h->begin_args;
     CK(cudaGraphAddKernelNode(&h->begin_node, graph, nullptr, 0, &kp));
-    // WHILE node over one iteration
     cudaGraphConditionalHandle cond;
     CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp{};
@@ -229,23 +241,35 @@ int build_graph(admm_handle *h)
     bp.gridDim = dim3(h->nblk_branch);
     bp.blockDim = dim3(kBranchBlock);
     bp.kernelParams = bargs;
-    cudaGraphNode_t bnode, unode, fnode;
+    cudaGraphNode_t bnode, unode, cnode, fnode, pnode;
     CK(cudaGraphAddKernelNode(&bnode, body, nullptr, 0, &bp));
-    int32_t use_cond = 1;
-    void *uargs[4] = {&h->G, &h->O, &cond, &use_cond};
     cudaKernelNodeParams up{};
     up.func = (void *)bus_dual_kernel;
     up.gridDim = dim3(h->nblk_bus);
     up.blockDim = dim3(kBusBlock);
-    up.kernelParams = uargs;
+    up.kernelParams = bargs;
     CK(cudaGraphAddKernelNode(&unode, body, &bnode, 1, &up));
-    void *fargs[2] = {&h->G, &h->O};
+    int32_t use_cond = 1;
+    void *cargs[3] = {&h->G, &cond, &use_cond};
+    cudaKernelNodeParams ccp{};
+    ccp.func = (void *)control_kernel;
+    ccp.gridDim = dim3(1);
+    ccp.blockDim = dim3(32);
+    ccp.kernelParams = cargs;
+    CK(cudaGraphAddKernelNode(&cnode, body, &unode, 1, &ccp));
     cudaKernelNodeParams fp{};
     fp.func = (void *)flush_lambda_kernel;
     fp.gridDim = dim3(h->nblk_flush);
     fp.blockDim = dim3(256);
-    fp.kernelParams = fargs;
+    fp.kernelParams = bargs;
     CK(cudaGraphAddKernelNode(&fnode, graph, &wnode, 1, &fp));
+    void *pargs[1] = {&h->G};
+    cudaKernelNodeParams pp{};
+    pp.func = (void *)clear_pending_kernel;
+    pp.gridDim = dim3((h->S + 255) / 256);
+    pp.blockDim = dim3(256);
+    pp.kernelParams = pargs;
+    CK(cudaGraphAddKernelNode(&pnode, graph, &fnode, 1, &pp));
     CK(cudaGraphInstantiate(&h->exec, graph, 0));
     h->graph_ok = true;
     return ADMM_OK;
@@ -260,32 +284,123 @@ void destroy_graph(admm_handle *h)
     h->graph_ok = false;
 }
 
-int cold_start(admm_handle *h)
+int cold_start(admm_handle *h, int s, double rho_va)
 {
-    double beta_init = h->opts.beta0 > 0.0 ? h->opts.beta0 : 10.0 * h->opts.rho_va;
-    cold_start_kernel<<<h->nblk_cold, 256, 0, h->stream>>>(h->G, beta_init);
+    const Range R = range_of(h, s);
+    const double beta_init = h->opts.beta0 > 0.0 ? h->opts.beta0 : 10.0 * rho_va;
+    const int n = (R.b1 - R.b0) + (R.k1 - R.k0) + (R.i1 - R.i0) + (R.g1 - R.g0) + 1;
+    cold_start_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(h->G, R, beta_init);
     return launch_check("cold_start_kernel");
+}
+
+int slot_begin(admm_handle *h, int s0, int s1, double rho_pq, double rho_va, double tol,
+               int32_t max_iter, int32_t warm)
+{
+    int rc;
+    if (!warm)
+        for (int s = s0; s < s1; ++s)
+            if ((rc = cold_start(h, s, rho_va)) != ADMM_OK) return rc;
+    SolveParams sp{tol, rho_pq, rho_va, max_iter, warm};
+    slot_begin_kernel<<<(s1 - s0 + 255) / 256, 256, 0, h->stream>>>(h->G, h->O, s0, s1, sp);
+    return launch_check("slot_begin_kernel");
+}
+
+// one run of the loop over the active scenarios, at most run_max iterations
+int run_async(admm_handle *h, int32_t run_max)
+{
+    int rc;
+    if (h->opts.use_graph && h->graph_ok) {
+        h->begin_run_max = run_max;
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)run_begin_kernel;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = h->begin_args;
+        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->begin_node, &kp));
+        CK(cudaGraphLaunch(h->exec, h->stream));
+        return ADMM_OK;
+    }
+    run_begin_kernel<<<1, 32, 0, h->stream>>>(h->G, run_max);
+    if ((rc = launch_check("run_begin_kernel")) != ADMM_OK) return rc;
+    cudaGraphConditionalHandle none = 0;
+    for (int it = 0; it < run_max; ++it) {
+        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
+        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
+        control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
+        if ((rc = launch_check("iteration kernels")) != ADMM_OK) return rc;
+        // poll the device flag now and then so a finished run stops enqueuing
+        if ((it & 63) == 63) {
+            CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (h->hctrl->done) break;
+        }
+    }
+    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
+    clear_pending_kernel<<<(h->S + 255) / 256, 256, 0, h->stream>>>(h->G);
+    return launch_check("flush_lambda_kernel");
+}
+
+int sync_sc(admm_handle *h)
+{
+    CK(cudaMemcpyAsync(h->hsc, h->G.sc, sizeof(SCtrl) * h->S, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADMM_OK;
 }
 
 }  // namespace
 
-extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handle **out)
+extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const admm_options *o,
+                                 admm_handle **out)
 {
     if (!out) { set_err("out is NULL"); return ADMM_ERR_INVALID_ARG; }
     *out = nullptr;
-    int rc = validate(g, o);
-    if (rc != ADMM_OK) return rc;
+    if (!grids || nscen < 1) { set_err("need at least one grid"); return ADMM_ERR_INVALID_ARG; }
+    int rc;
+    long long tot_nb = 0, tot_nl = 0, tot_ng = 0;
+    for (int s = 0; s < nscen; ++s) {
+        if ((rc = validate(&grids[s], o)) != ADMM_OK) {
+            g_err = "scenario " + std::to_string(s) + ": " + g_err;
+            return rc;
+        }
+        tot_nb += grids[s].nbus; tot_nl += grids[s].nbranch; tot_ng += grids[s].ngen;
+    }
+    if (8 * tot_nl + 2 * tot_ng > 0x7fffffffLL || 2 * tot_nl + tot_ng > 0x7fffffffLL) {
+        set_err("batch too large");
+        return ADMM_ERR_INVALID_ARG;
+    }
     admm_handle *h = new admm_handle();
     if (o) h->opts = *o; else admm_default_options(&h->opts);
     const admm_options &op = h->opts;
-    h->nb = g->nbus; h->nl = g->nbranch; h->ng = g->ngen; h->ref = g->ref_bus;
+    const int S = nscen;
+    h->S = S;
+    h->nb = (int)tot_nb; h->nl = (int)tot_nl; h->ng = (int)tot_ng;
     h->ns = 2 * h->nl + h->ng;
-    h->base = g->base_mva;
     const int nb = h->nb, nl = h->nl, ng = h->ng, ns = h->ns;
+    h->bus_off.assign(S + 1, 0); h->br_off.assign(S + 1, 0); h->gen_off.assign(S + 1, 0);
+    h->slot_off.assign(S + 1, 0); h->blk_off.assign(S + 1, 0);
+    h->base_mva.resize(S);
+    for (int s = 0; s < S; ++s) {
+        h->bus_off[s + 1] = h->bus_off[s] + grids[s].nbus;
+        h->br_off[s + 1] = h->br_off[s] + grids[s].nbranch;
+        h->gen_off[s + 1] = h->gen_off[s] + grids[s].ngen;
+        h->blk_off[s + 1] = h->blk_off[s] + (grids[s].nbus + kBusBlock - 1) / kBusBlock;
+        h->base_mva[s] = grids[s].base_mva;
+    }
+    // concatenated topology in global indices
+    h->f_bus.resize(nl); h->t_bus.resize(nl); h->gen_bus.resize(ng);
+    std::vector<int32_t> br_scen(nl), blk_scen(h->blk_off[S]), slot_scen(ns);
+    for (int s = 0; s < S; ++s) {
+        const admm_grid &g = grids[s];
+        for (int l = 0; l < g.nbranch; ++l) {
+            h->f_bus[h->br_off[s] + l] = h->bus_off[s] + g.f_bus[l];
+            h->t_bus[h->br_off[s] + l] = h->bus_off[s] + g.t_bus[l];
+            br_scen[h->br_off[s] + l] = s;
+        }
+        for (int k = 0; k < g.ngen; ++k) h->gen_bus[h->gen_off[s] + k] = h->bus_off[s] + g.gen_bus[k];
+        for (int b = h->blk_off[s]; b < h->blk_off[s + 1]; ++b) blk_scen[b] = s;
+    }
     // CSR bus -> incident entries by a stable counting sort over entry ids
-    h->f_bus.assign(g->f_bus, g->f_bus + nl);
-    h->t_bus.assign(g->t_bus, g->t_bus + nl);
-    h->gen_bus.assign(g->gen_bus ? g->gen_bus : nullptr, g->gen_bus ? g->gen_bus + ng : nullptr);
     h->row_ptr.assign(nb + 1, 0);
     h->col.assign(ns, 0);
     auto bus_of = [&](int e) { return e < 2 * nl ? ((e & 1) ? h->t_bus[e >> 1] : h->f_bus[e >> 1]) : h->gen_bus[e - 2 * nl]; };
@@ -295,6 +410,9 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
         std::vector<int32_t> fill(h->row_ptr.begin(), h->row_ptr.end() - 1);
         for (int e = 0; e < ns; ++e) h->col[fill[bus_of(e)]++] = e;
     }
+    for (int s = 0; s <= S; ++s) h->slot_off[s] = h->row_ptr[h->bus_off[s]];
+    for (int s = 0; s < S; ++s)
+        for (int k = h->slot_off[s]; k < h->slot_off[s + 1]; ++k) slot_scen[k] = s;
     {
         // branch_tron is persistent: at most kBranchBlocksPerSM blocks per SM
         int dev = 0, sms = 0;
@@ -303,12 +421,16 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
             sms = 152;
         cudaGetLastError();
         const int need = (nl + kBranchBlock - 1) / kBranchBlock;
-        const int cap = h->opts.branch_blocks > 0 ? h->opts.branch_blocks : sms * kBranchBlocksPerSM;
+        const int cap = op.branch_blocks > 0 ? op.branch_blocks : sms * kBranchBlocksPerSM;
         h->nblk_branch = need < cap ? need : cap;
     }
-    h->nblk_bus = (nb + kBusBlock - 1) / kBusBlock;
-    h->nblk_cold = (nl + ns + nb + ng + 1 + 255) / 256;
-    h->nblk_fin = (nb + nl + ng + kFinBlock - 1) / kFinBlock;
+    h->nblk_bus = h->blk_off[S];
+    int maxfin = 1;
+    for (int s = 0; s < S; ++s) {
+        const int n = (grids[s].nbus + grids[s].nbranch + grids[s].ngen + kFinBlock - 1) / kFinBlock;
+        maxfin = n > maxfin ? n : maxfin;
+    }
+    h->nblk_fin = maxfin;
     h->nblk_flush = (4 * ns + 255) / 256 < 1184 ? (4 * ns + 255) / 256 : 1184;
     // device layout
     Carver cv;
@@ -329,7 +451,16 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     size_t o_part = cv.take<double>(8 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
     size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
     size_t o_ctrl = cv.take<Ctrl>(1);
-    size_t o_out = cv.take<double>(2 * (size_t)nb + 4 * (size_t)nl + 2 * (size_t)ng + 1);
+    size_t o_sc = cv.take<SCtrl>(S);
+    size_t o_offs = cv.take<int32_t>(5 * (size_t)(S + 1));
+    size_t o_blks = cv.take<int32_t>(h->nblk_bus), o_brs = cv.take<int32_t>(nl), o_sls = cv.take<int32_t>(ns);
+    int maxnb = 1, maxnl = 1, maxng = 1;
+    for (int s = 0; s < S; ++s) {
+        maxnb = grids[s].nbus > maxnb ? grids[s].nbus : maxnb;
+        maxnl = grids[s].nbranch > maxnl ? grids[s].nbranch : maxnl;
+        maxng = grids[s].ngen > maxng ? grids[s].ngen : maxng;
+    }
+    size_t o_out = cv.take<double>(2 * (size_t)maxnb + 4 * (size_t)maxnl + 2 * (size_t)maxng + 1);
     h->dbytes = cv.off;
     cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
     if (e != cudaSuccess) {
@@ -337,16 +468,15 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
         delete h;
         return e == cudaErrorMemoryAllocation ? ADMM_ERR_OOM : ADMM_ERR_CUDA;
     }
-    e = cudaMallocHost(&h->hctrl, sizeof(Ctrl));
-    if (e != cudaSuccess) {
-        set_err("cudaMallocHost failed: %s", cudaGetErrorString(e));
-        cudaFree(h->dmem);
-        delete h;
+    if (cudaMallocHost(&h->hctrl, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMallocHost(&h->hsc, sizeof(SCtrl) * S) != cudaSuccess) {
+        set_err("cudaMallocHost failed");
+        admm_destroy(h);
         return ADMM_ERR_CUDA;
     }
     char *base = (char *)h->dmem;
     DevGrid &G = h->G;
-    G.nb = nb; G.nl = nl; G.ng = ng; G.ns = ns; G.ref = h->ref;
+    G.nb = nb; G.nl = nl; G.ng = ng; G.ns = ns; G.S = S;
     G.nblk_bus = h->nblk_bus;
     G.nblk_branch = h->nblk_branch;
     G.f_bus = (int32_t *)(base + o_fb); G.t_bus = (int32_t *)(base + o_tb);
@@ -365,6 +495,12 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     G.partials = (double *)(base + o_part); G.fin_partials = (double *)(base + o_fpart);
     G.hist = (double *)(base + o_hist);
     G.ctrl = (Ctrl *)(base + o_ctrl);
+    G.sc = (SCtrl *)(base + o_sc);
+    int32_t *offs = (int32_t *)(base + o_offs);
+    G.bus_off = offs; G.br_off = offs + (S + 1); G.gen_off = offs + 2 * (S + 1);
+    G.slot_off = offs + 3 * (S + 1); G.blk_off = offs + 4 * (S + 1);
+    G.blk_scen = (int32_t *)(base + o_blks); G.br_scen = (int32_t *)(base + o_brs);
+    G.slot_scen = (int32_t *)(base + o_sls);
     G.line_limit_frac = op.line_limit_frac;
     h->dout = (double *)(base + o_out);
     DevOpts &O = h->O;
@@ -378,40 +514,66 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     O.two_level = op.two_level; O.max_outer = op.max_outer; O.max_inner = op.max_inner;
     O.al_max_iter = op.al_max_iter; O.tron_max_iter = op.tron_max_iter;
     // uploads (host staging in the device layout)
-    auto fail = [&](int code) { admm_destroy(h); return code; };
     {
-        std::vector<double> bus(6 * (size_t)nb), raw(6 * (size_t)nl), gc(3 * (size_t)ng + 1), glim(4 * (size_t)ng + 1);
-        const double *ba[6] = {g->pd, g->qd, g->gs, g->bs, g->vmin, g->vmax};
-        for (int k = 0; k < 6; ++k) std::memcpy(&bus[(size_t)k * nb], ba[k], sizeof(double) * nb);
-        const double *ra[6] = {g->r, g->x, g->b, g->tap, g->shift, g->rate_a};
-        for (int k = 0; k < 6; ++k) std::memcpy(&raw[(size_t)k * nl], ra[k], sizeof(double) * nl);
-        for (int k = 0; k < ng; ++k) {
-            gc[k] = g->c2[k] * h->base * h->base;
-            gc[ng + k] = g->c1[k] * h->base;
-            gc[2 * ng + k] = g->c0[k];
-            glim[k] = g->pmin[k];
-            glim[ng + k] = g->pmax[k];
-            glim[2 * ng + k] = g->qmin[k];
-            glim[3 * ng + k] = g->qmax[k];
+        std::vector<double> bus(6 * (size_t)nb), raw(6 * (size_t)nl), gc(3 * (size_t)ng + 1),
+            glim(4 * (size_t)ng + 1);
+        std::vector<SCtrl> sc(S);
+        for (int s = 0; s < S; ++s) {
+            const admm_grid &g = grids[s];
+            const int i0 = h->bus_off[s], l0 = h->br_off[s], k0 = h->gen_off[s];
+            const double *ba[6] = {g.pd, g.qd, g.gs, g.bs, g.vmin, g.vmax};
+            for (int k = 0; k < 6; ++k)
+                std::memcpy(&bus[(size_t)k * nb + i0], ba[k], sizeof(double) * g.nbus);
+            const double *ra[6] = {g.r, g.x, g.b, g.tap, g.shift, g.rate_a};
+            for (int k = 0; k < 6; ++k)
+                std::memcpy(&raw[(size_t)k * nl + l0], ra[k], sizeof(double) * g.nbranch);
+            for (int k = 0; k < g.ngen; ++k) {
+                const int q = k0 + k;
+                gc[q] = g.c2[k] * g.base_mva * g.base_mva;
+                gc[ng + q] = g.c1[k] * g.base_mva;
+                gc[2 * (size_t)ng + q] = g.c0[k];
+                glim[q] = g.pmin[k];
+                glim[ng + q] = g.pmax[k];
+                glim[2 * (size_t)ng + q] = g.qmin[k];
+                glim[3 * (size_t)ng + q] = g.qmax[k];
+            }
+            std::memset(&sc[s], 0, sizeof(SCtrl));
+            sc[s].ref = i0 + g.ref_bus;
+            sc[s].m = 2 * g.ngen + 8 * g.nbranch;
+            sc[s].done = 1;
+            sc[s].rho_pq = op.rho_pq;
+            sc[s].rho_va = op.rho_va;
         }
-        if (cudaMemset(h->dmem, 0, h->dbytes) != cudaSuccess ||
-            cudaMemcpy(G.bus, bus.data(), bus.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy((void *)G.raw, raw.data(), raw.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(G.gc, gc.data(), gc.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(G.glim, glim.data(), glim.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(G.gbase, glim.data(), 2 * (size_t)ng * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy((void *)G.f_bus, g->f_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy((void *)G.t_bus, g->t_bus, nl * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-            (ng > 0 && cudaMemcpy((void *)G.gen_bus, g->gen_bus, ng * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) ||
-            cudaMemcpy((void *)G.row_ptr, h->row_ptr.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy((void *)G.col, h->col.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        std::vector<int32_t> offv(5 * (size_t)(S + 1));
+        for (int s = 0; s <= S; ++s) {
+            offv[s] = h->bus_off[s];
+            offv[(S + 1) + s] = h->br_off[s];
+            offv[2 * (S + 1) + s] = h->gen_off[s];
+            offv[3 * (S + 1) + s] = h->slot_off[s];
+            offv[4 * (S + 1) + s] = h->blk_off[s];
+        }
+        auto up = [&](void *dst, const void *src, size_t bytes) {
+            return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        };
+        if (cudaMemset(h->dmem, 0, h->dbytes) != cudaSuccess || !up(G.bus, bus.data(), bus.size() * 8) ||
+            !up((void *)G.raw, raw.data(), raw.size() * 8) || !up(G.gc, gc.data(), gc.size() * 8) ||
+            !up(G.glim, glim.data(), glim.size() * 8) || !up(G.gbase, glim.data(), 2 * (size_t)ng * 8) ||
+            !up((void *)G.f_bus, h->f_bus.data(), nl * 4) || !up((void *)G.t_bus, h->t_bus.data(), nl * 4) ||
+            !up((void *)G.gen_bus, h->gen_bus.data(), (size_t)ng * 4) ||
+            !up((void *)G.row_ptr, h->row_ptr.data(), (nb + 1) * 4) || !up((void *)G.col, h->col.data(), ns * 4) ||
+            !up(G.sc, sc.data(), sizeof(SCtrl) * S) || !up(offs, offv.data(), offv.size() * 4) ||
+            !up((void *)G.blk_scen, blk_scen.data(), blk_scen.size() * 4) ||
+            !up((void *)G.br_scen, br_scen.data(), br_scen.size() * 4) ||
+            !up((void *)G.slot_scen, slot_scen.data(), slot_scen.size() * 4)) {
             set_err("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
-            return fail(ADMM_ERR_CUDA);
+            admm_destroy(h);
+            return ADMM_ERR_CUDA;
         }
     }
     admittance_kernel<<<(nl + 255) / 256, 256, 0, h->stream>>>(G);
-    if ((rc = launch_check("admittance_kernel")) != ADMM_OK) return fail(rc);
-    if ((rc = cold_start(h)) != ADMM_OK) return fail(rc);
+    if ((rc = launch_check("admittance_kernel")) != ADMM_OK) { admm_destroy(h); return rc; }
+    for (int s = 0; s < S; ++s)
+        if ((rc = cold_start(h, s, op.rho_va)) != ADMM_OK) { admm_destroy(h); return rc; }
     if (op.use_graph) {
         rc = build_graph(h);
         if (rc != ADMM_OK) {
@@ -423,10 +585,17 @@ extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handl
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
         set_err("setup failed: %s", cudaGetErrorString(cudaGetLastError()));
-        return fail(ADMM_ERR_CUDA);
+        admm_destroy(h);
+        return ADMM_ERR_CUDA;
     }
     *out = h;
     return ADMM_OK;
+}
+
+extern "C" int admm_create(const admm_grid *g, const admm_options *o, admm_handle **out)
+{
+    if (!g) { set_err("grid is NULL"); return ADMM_ERR_INVALID_ARG; }
+    return admm_create_batch(g, 1, o, out);
 }
 
 extern "C" void admm_destroy(admm_handle *h)
@@ -437,7 +606,17 @@ extern "C" void admm_destroy(admm_handle *h)
     destroy_graph(h);
     if (h->dmem) cudaFree(h->dmem);
     if (h->hctrl) cudaFreeHost(h->hctrl);
+    if (h->hsc) cudaFreeHost(h->hsc);
     delete h;
+}
+
+extern "C" int32_t admm_scenario_count(admm_handle *h) { return h ? h->S : 0; }
+
+extern "C" int admm_select_scenario(admm_handle *h, int32_t s)
+{
+    if (!h || s < 0 || s >= h->S) { set_err("scenario out of range"); return ADMM_ERR_INVALID_ARG; }
+    h->sel = s;
+    return ADMM_OK;
 }
 
 extern "C" int admm_set_stream(admm_handle *h, void *s)
@@ -450,32 +629,37 @@ extern "C" int admm_set_stream(admm_handle *h, void *s)
 extern "C" int admm_set_loads(admm_handle *h, const double *pd, const double *qd)
 {
     if (!h || !pd || !qd) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    if (!finite_all(pd, h->nb) || !finite_all(qd, h->nb)) { set_err("loads not finite"); return ADMM_ERR_INVALID_ARG; }
-    CK(cudaMemcpyAsync(h->G.bus, pd, sizeof(double) * h->nb, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->G.bus + h->nb, qd, sizeof(double) * h->nb, cudaMemcpyHostToDevice, h->stream));
+    const int i0 = h->bus_off[h->sel], n = h->bus_off[h->sel + 1] - i0;
+    if (!finite_all(pd, n) || !finite_all(qd, n)) { set_err("loads not finite"); return ADMM_ERR_INVALID_ARG; }
+    CK(cudaMemcpyAsync(h->G.bus + i0, pd, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.bus + h->nb + i0, qd, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     return ADMM_OK;
 }
 
 extern "C" int admm_set_loads_device(admm_handle *h, const double *d_pd, const double *d_qd)
 {
     if (!h || !d_pd || !d_qd) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    CK(cudaMemcpyAsync(h->G.bus, d_pd, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->G.bus + h->nb, d_qd, sizeof(double) * h->nb, cudaMemcpyDeviceToDevice, h->stream));
+    const int i0 = h->bus_off[h->sel], n = h->bus_off[h->sel + 1] - i0;
+    CK(cudaMemcpyAsync(h->G.bus + i0, d_pd, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.bus + h->nb + i0, d_qd, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
     return ADMM_OK;
 }
 
 extern "C" int admm_set_gen_bounds(admm_handle *h, const double *pmin, const double *pmax)
 {
     if (!h || !pmin || !pmax) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    for (int k = 0; k < h->ng; ++k)
+    const int g0 = h->gen_off[h->sel], n = h->gen_off[h->sel + 1] - g0;
+    for (int k = 0; k < n; ++k)
         if (!(pmin[k] <= pmax[k]) || !std::isfinite(pmin[k]) || !std::isfinite(pmax[k])) {
             set_err("generator %d: empty or non-finite bounds", k);
             return ADMM_ERR_INVALID_ARG;
         }
-    if (h->ng == 0) return ADMM_OK;
-    CK(cudaMemcpyAsync(h->G.glim, pmin, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->G.glim + h->ng, pmax, sizeof(double) * h->ng, cudaMemcpyHostToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->G.gbase, h->G.glim, sizeof(double) * 2 * h->ng, cudaMemcpyDeviceToDevice, h->stream));
+    if (n == 0) return ADMM_OK;
+    const int ng = h->ng;
+    CK(cudaMemcpyAsync(h->G.glim + g0, pmin, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.glim + ng + g0, pmax, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.gbase + g0, pmin, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->G.gbase + ng + g0, pmax, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
     return ADMM_OK;
 }
 
@@ -483,8 +667,9 @@ extern "C" int admm_set_ramp_limit(admm_handle *h, double frac)
 {
     if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
     if (!(frac >= 0.0) || !std::isfinite(frac)) { set_err("ramp fraction must be >= 0"); return ADMM_ERR_INVALID_ARG; }
-    if (h->ng == 0) return ADMM_OK;
-    ramp_limit_kernel<<<(h->ng + 255) / 256, 256, 0, h->stream>>>(h->G, frac);
+    const Range R = range_of(h, h->sel);
+    if (R.g1 == R.g0) return ADMM_OK;
+    ramp_limit_kernel<<<(R.g1 - R.g0 + 255) / 256, 256, 0, h->stream>>>(h->G, R, frac);
     return launch_check("ramp_limit_kernel");
 }
 
@@ -498,40 +683,10 @@ extern "C" int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, do
     }
     h->opts.rho_pq = rho_pq;
     h->opts.rho_va = rho_va;
-    int rc;
-    if (!warm_start && (rc = cold_start(h)) != ADMM_OK) return rc;
-    SolveParams sp{tol, rho_pq, rho_va, max_iter, warm_start};
-    if (max_iter == 0) {
-        begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
-        return launch_check("begin_kernel");
-    }
-    if (h->opts.use_graph && h->graph_ok) {
-        h->begin_params = sp;
-        cudaKernelNodeParams kp{};
-        kp.func = (void *)begin_kernel;
-        kp.gridDim = dim3(1);
-        kp.blockDim = dim3(32);
-        kp.kernelParams = h->begin_args;
-        CK(cudaGraphExecKernelNodeSetParams(h->exec, h->begin_node, &kp));
-        CK(cudaGraphLaunch(h->exec, h->stream));
-        return ADMM_OK;
-    }
-    begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
-    if ((rc = launch_check("begin_kernel")) != ADMM_OK) return rc;
-    cudaGraphConditionalHandle none = 0;
-    for (int it = 0; it < max_iter; ++it) {
-        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
-        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O, none, 0);
-        if ((rc = launch_check("iteration kernels")) != ADMM_OK) return rc;
-        // poll the device flag now and then so a converged solve stops enqueuing
-        if ((it & 63) == 63) {
-            CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-            CK(cudaStreamSynchronize(h->stream));
-            if (h->hctrl->done) break;
-        }
-    }
-    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
-    return launch_check("flush_lambda_kernel");
+    int rc = slot_begin(h, 0, h->S, rho_pq, rho_va, tol, max_iter, warm_start);
+    if (rc != ADMM_OK) return rc;
+    if (max_iter == 0) return ADMM_OK;
+    return run_async(h, max_iter);
 }
 
 extern "C" int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
@@ -539,24 +694,58 @@ extern "C" int admm_solve(admm_handle *h, double rho_pq, double rho_va, double t
 {
     int rc = admm_solve_async(h, rho_pq, rho_va, tol, max_iter, warm_start);
     if (rc != ADMM_OK) return rc;
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    int st = h->hctrl->status;
-    if (max_iter == 0) st = ADMM_NOT_CONVERGED;
-    h->last_status = st;
+    if ((rc = sync_sc(h)) != ADMM_OK) return rc;
+    int st = ADMM_OK;
+    for (int s = 0; s < h->S; ++s) {
+        int q = h->hsc[s].status == CS_RUNNING ? ADMM_NOT_CONVERGED : h->hsc[s].status;
+        if (max_iter == 0) q = ADMM_NOT_CONVERGED;
+        if (q < 0) st = q < st ? q : st;
+        else if (st >= 0 && q > st) st = q;
+    }
     return st;
+}
+
+extern "C" int admm_slot_begin(admm_handle *h, int32_t s, double rho_pq, double rho_va, double tol,
+                               int32_t max_iter, int32_t warm_start)
+{
+    if (!h || s < 0 || s >= h->S) { set_err("scenario out of range"); return ADMM_ERR_INVALID_ARG; }
+    if (!(rho_pq > 0.0) || !(rho_va > 0.0) || !(tol >= 0.0) || max_iter < 0) {
+        set_err("need rho > 0, tol >= 0, max_iter >= 0");
+        return ADMM_ERR_INVALID_ARG;
+    }
+    return slot_begin(h, s, s + 1, rho_pq, rho_va, tol, max_iter, warm_start);
+}
+
+extern "C" int admm_run(admm_handle *h, int32_t max_iters)
+{
+    if (!h || max_iters < 0) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    if (max_iters == 0) return ADMM_OK;
+    return run_async(h, max_iters);
+}
+
+extern "C" int admm_slot_status(admm_handle *h, int32_t *status, int32_t *iters)
+{
+    if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
+    for (int s = 0; s < h->S; ++s) {
+        const SCtrl &c = h->hsc[s];
+        if (status) status[s] = !c.done ? CS_RUNNING : c.status == CS_RUNNING ? ADMM_NOT_CONVERGED : c.status;
+        if (iters) iters[s] = c.iter;
+    }
+    return ADMM_OK;
 }
 
 extern "C" int admm_get_residuals(admm_handle *h, admm_residuals *out)
 {
     if (!h || !out) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    const Ctrl &c = *h->hctrl;
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
+    const SCtrl &c = h->hsc[h->sel];
     out->iters = c.iter;
     out->outer_iters = c.outer;
     out->status = c.status == CS_RUNNING ? ADMM_NOT_CONVERGED : c.status;
-    out->tron_failures = (int32_t)c.stats[ST_TRON_MAXHIT];
+    out->tron_failures = (int32_t)h->hctrl->stats[ST_TRON_MAXHIT];
     out->primal_res = c.pri;
     out->dual_res = c.dual;
     out->z_norm = c.zn;
@@ -564,8 +753,8 @@ extern "C" int admm_get_residuals(admm_handle *h, admm_residuals *out)
     out->beta = c.beta;
     out->eps_pri = c.eps_pri;
     out->eps_dual = c.eps_dual;
-    out->objective = h->last_obj;
-    out->max_viol = h->last_viol;
+    out->objective = c.objective;
+    out->max_viol = c.max_viol;
     return ADMM_OK;
 }
 
@@ -573,12 +762,14 @@ extern "C" int admm_get_solution(admm_handle *h, double *pg, double *qg, double 
                                  double *pf, double *qf, double *pt, double *qt)
 {
     if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
-    const int nb = h->nb, nl = h->nl, ng = h->ng;
+    const Range R = range_of(h, h->sel);
+    const int nb = R.i1 - R.i0, nl = R.b1 - R.b0, ng = R.g1 - R.g0;
     double *d = h->dout;
     double *dvm = d, *dva = d + nb, *dpf = d + 2 * nb, *dqf = dpf + nl, *dpt = dqf + nl,
            *dqt = dpt + nl, *dpg = dqt + nl, *dqg = dpg + ng;
-    finalize_kernel<<<h->nblk_fin, kFinBlock, 0, h->stream>>>(h->G, dpg, dqg, dvm, dva, dpf, dqf,
-                                                              dpt, dqt, h->nblk_fin);
+    const int nblk = (nb + nl + ng + kFinBlock - 1) / kFinBlock;
+    finalize_kernel<<<nblk, kFinBlock, 0, h->stream>>>(h->G, R, dpg, dqg, dvm, dva, dpf, dqf, dpt,
+                                                       dqt, nblk);
     int rc = launch_check("finalize_kernel");
     if (rc != ADMM_OK) return rc;
     struct { double *host; const double *dev; int n; } cp[] = {
@@ -587,35 +778,24 @@ extern "C" int admm_get_solution(admm_handle *h, double *pg, double *qg, double 
     for (auto &c : cp)
         if (c.host && c.n > 0)
             CK(cudaMemcpyAsync(c.host, c.dev, sizeof(double) * c.n, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    h->last_obj = h->hctrl->objective;
-    h->last_viol = h->hctrl->max_viol;
-    return ADMM_OK;
+    return sync_sc(h);
 }
 
 extern "C" int32_t admm_get_history(admm_handle *h, double *out, int32_t cap)
 {
     if (!h || !out || cap < 0) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
-    if (cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess) {
-        set_err("history copy failed");
-        return ADMM_ERR_CUDA;
-    }
-    int n = h->hctrl->iter;
-    if (n > kHistCap) n = kHistCap;   // the ring keeps the last kHistCap rows
+    if (sync_sc(h) != ADMM_OK) return ADMM_ERR_CUDA;
+    const int total = h->hsc[0].iter;
+    int n = total > kHistCap ? kHistCap : total;   // the ring keeps the last kHistCap rows
     if (n > cap) n = cap;
     std::vector<double> all(4 * (size_t)kHistCap);
     if (cudaMemcpy(all.data(), h->G.hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
         set_err("history copy failed");
         return ADMM_ERR_CUDA;
     }
-    int total = h->hctrl->iter;
-    int first = total > kHistCap ? total - kHistCap : 0;
-    for (int r = 0; r < n; ++r) {
-        int it = first + r;
-        std::memcpy(out + 4 * (size_t)r, &all[4 * (size_t)(it % kHistCap)], 4 * sizeof(double));
-    }
+    const int first = total > kHistCap ? total - kHistCap : 0;
+    for (int r = 0; r < n; ++r)
+        std::memcpy(out + 4 * (size_t)r, &all[4 * (size_t)((first + r) % kHistCap)], 4 * sizeof(double));
     return n;
 }
 
@@ -635,16 +815,18 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
 {
     if (!h || !out) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
     const int nb = h->nb, nl = h->nl, ng = h->ng, ns = h->ns;
-    const size_t m = 2 * (size_t)ng + 8 * (size_t)nl;
-    std::vector<double> a, b, c, d;
+    const Range R = range_of(h, h->sel);
+    const int nls = R.b1 - R.b0, ngs = R.g1 - R.g0, nbs = R.i1 - R.i0;
+    std::vector<double> a, b, c;
     int rc = ADMM_OK;
-    auto cb = [&](int l, int k) { return 2 * (size_t)ng + 8 * (size_t)l + k; };
+    // canonical order within the scenario: its generators, then its branches
+    auto cb = [&](int l, int k) { return 2 * (size_t)ngs + 8 * (size_t)(l - R.b0) + k; };
     auto sync = [&]() -> int { CK(cudaStreamSynchronize(h->stream)); return ADMM_OK; };
     switch (which) {
     case ADMM_VEC_U:
         if ((rc = fetch(h, h->G.bu, 8 * (size_t)nl, a)) || (rc = fetch(h, h->G.gu, 2 * (size_t)ng, b)) || (rc = sync())) return rc;
-        for (int g = 0; g < ng; ++g) { out[2 * g] = b[g]; out[2 * g + 1] = b[ng + g]; }
-        for (int l = 0; l < nl; ++l)
+        for (int g = R.g0; g < R.g1; ++g) { out[2 * (g - R.g0)] = b[g]; out[2 * (g - R.g0) + 1] = b[ng + g]; }
+        for (int l = R.b0; l < R.b1; ++l)
             for (int k = 0; k < 8; ++k) out[cb(l, k)] = a[(size_t)k * nl + l];
         return ADMM_OK;
     case ADMM_VEC_XBAR:
@@ -659,13 +841,13 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
         } else if ((rc = fetch(h, src, 4 * (size_t)ns, a)) || (rc = sync())) {
             return rc;
         }
-        for (int i = 0; i < nb; ++i) {
+        for (int i = R.i0; i < R.i1; ++i) {
             for (int k = h->row_ptr[i]; k < h->row_ptr[i + 1]; ++k) {
-                int e = h->col[k];
+                const int e = h->col[k];
                 if (e < 2 * nl) {
-                    int l = e >> 1, end = e & 1;
-                    size_t cp = cb(l, end ? 2 : 0), cq = cb(l, end ? 3 : 1);
-                    size_t cw = cb(l, end ? 6 : 4), ct = cb(l, end ? 7 : 5);
+                    const int l = e >> 1, end = e & 1;
+                    const size_t cp = cb(l, end ? 2 : 0), cq = cb(l, end ? 3 : 1);
+                    const size_t cw = cb(l, end ? 6 : 4), ct = cb(l, end ? 7 : 5);
                     if (which == ADMM_VEC_XBAR) {
                         out[cp] = a[k]; out[cq] = a[ns + k]; out[cw] = b[i]; out[ct] = c[i];
                     } else {
@@ -673,7 +855,7 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
                         out[ct] = a[3 * (size_t)ns + k];
                     }
                 } else {
-                    int g = e - 2 * nl;
+                    const int g = e - 2 * nl - R.g0;
                     out[2 * g] = a[k];
                     out[2 * g + 1] = a[ns + k];
                 }
@@ -681,25 +863,27 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
         }
         return ADMM_OK;
     }
-    case ADMM_VEC_RHO:
-        for (int g = 0; g < ng; ++g) { out[2 * g] = h->opts.rho_pq; out[2 * g + 1] = h->opts.rho_pq; }
-        for (int l = 0; l < nl; ++l)
-            for (int k = 0; k < 8; ++k) out[cb(l, k)] = k < 4 ? h->opts.rho_pq : h->opts.rho_va;
-        (void)m;
+    case ADMM_VEC_RHO: {
+        if ((rc = sync_sc(h)) != ADMM_OK) return rc;
+        const double rp = h->hsc[h->sel].rho_pq, rv = h->hsc[h->sel].rho_va;
+        for (int g = 0; g < ngs; ++g) { out[2 * g] = rp; out[2 * g + 1] = rp; }
+        for (int l = R.b0; l < R.b1; ++l)
+            for (int k = 0; k < 8; ++k) out[cb(l, k)] = k < 4 ? rp : rv;
         return ADMM_OK;
+    }
     case ADMM_VEC_BRANCH_X:
     case ADMM_VEC_BRANCH_LT:
     case ADMM_VEC_ADMITTANCE: {
-        int w = which == ADMM_VEC_BRANCH_X ? 6 : which == ADMM_VEC_BRANCH_LT ? 2 : 8;
+        const int w = which == ADMM_VEC_BRANCH_X ? 6 : which == ADMM_VEC_BRANCH_LT ? 2 : 8;
         const double *src = which == ADMM_VEC_BRANCH_X ? h->G.bx : which == ADMM_VEC_BRANCH_LT ? h->G.blt : h->G.Y;
         if ((rc = fetch(h, src, (size_t)w * nl, a)) || (rc = sync())) return rc;
-        for (int l = 0; l < nl; ++l)
-            for (int k = 0; k < w; ++k) out[(size_t)l * w + k] = a[(size_t)k * nl + l];
+        for (int l = R.b0; l < R.b1; ++l)
+            for (int k = 0; k < w; ++k) out[(size_t)(l - R.b0) * w + k] = a[(size_t)k * nl + l];
         return ADMM_OK;
     }
     case ADMM_VEC_BUS:
         if ((rc = fetch(h, h->G.bw, nb, a)) || (rc = fetch(h, h->G.bth, nb, b)) || (rc = sync())) return rc;
-        for (int i = 0; i < nb; ++i) { out[2 * i] = a[i]; out[2 * i + 1] = b[i]; }
+        for (int i = 0; i < nbs; ++i) { out[2 * i] = a[R.i0 + i]; out[2 * i + 1] = b[R.i0 + i]; }
         return ADMM_OK;
     default:
         set_err("unknown vector id %d", which);
@@ -710,16 +894,21 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
 extern "C" int admm_get_csr(admm_handle *h, int32_t *row_ptr, int32_t *col)
 {
     if (!h || !row_ptr || !col) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    std::memcpy(row_ptr, h->row_ptr.data(), sizeof(int32_t) * (h->nb + 1));
-    std::memcpy(col, h->col.data(), sizeof(int32_t) * h->ns);
+    const Range R = range_of(h, h->sel);
+    const int nls = R.b1 - R.b0;
+    for (int i = R.i0; i <= R.i1; ++i) row_ptr[i - R.i0] = h->row_ptr[i] - R.k0;
+    for (int k = R.k0; k < R.k1; ++k) {
+        const int e = h->col[k];
+        col[k - R.k0] = e < 2 * h->nl ? e - 2 * R.b0 : 2 * nls + (e - 2 * h->nl - R.g0);
+    }
     return ADMM_OK;
 }
 
 extern "C" int admm_get_stats(admm_handle *h, int64_t *out9)
 {
     if (!h || !out9) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
     for (int k = 0; k < kNumStats; ++k) out9[k] = (int64_t)h->hctrl->stats[k];
     return ADMM_OK;
 }
@@ -740,6 +929,8 @@ std::vector<StatePart> state_parts(admm_handle *h)
             {h->G.sz, 4 * ns}, {h->G.sy, 4 * ns},  {h->G.sl, 4 * ns}};
 }
 
+constexpr int kScalarsPerScenario = 4;   // beta, total iterations, beta_used, pending
+
 }  // namespace
 
 extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
@@ -748,19 +939,24 @@ extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
     auto parts = state_parts(h);
     size_t n = 0;
     for (auto &p : parts) n += p.n;
-    const size_t need = 4 * sizeof(uint64_t) + 4 * sizeof(double) + n * sizeof(double);
+    const size_t need = 5 * sizeof(uint64_t) + kScalarsPerScenario * (size_t)h->S * sizeof(double) +
+                        n * sizeof(double);
     if (!buf) { *len = need; return ADMM_OK; }
     if (*len < need) { set_err("state buffer too small (%zu < %zu)", *len, need); return ADMM_ERR_INVALID_ARG; }
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
     uint64_t *hdr = (uint64_t *)buf;
     hdr[0] = kStateMagic; hdr[1] = (uint64_t)h->nb; hdr[2] = (uint64_t)h->nl; hdr[3] = (uint64_t)h->ng;
-    double *sc = (double *)(hdr + 4);
-    sc[0] = h->hctrl->beta;
-    sc[1] = (double)h->hctrl->total_iters;
-    sc[2] = h->hctrl->pending ? h->hctrl->beta_used : 0.0;
-    sc[3] = (double)h->hctrl->pending;
-    double *p = sc + 4;
+    hdr[4] = (uint64_t)h->S;
+    double *sc = (double *)(hdr + 5);
+    for (int s = 0; s < h->S; ++s) {
+        const SCtrl &c = h->hsc[s];
+        sc[4 * s] = c.beta;
+        sc[4 * s + 1] = (double)c.total_iters;
+        sc[4 * s + 2] = c.pending ? c.beta_used : 0.0;
+        sc[4 * s + 3] = (double)c.pending;
+    }
+    double *p = sc + kScalarsPerScenario * h->S;
     for (auto &pt : parts) {
         if (pt.n) CK(cudaMemcpyAsync(p, pt.dev, pt.n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         p += pt.n;
@@ -776,27 +972,31 @@ extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
     auto parts = state_parts(h);
     size_t n = 0;
     for (auto &p : parts) n += p.n;
-    const size_t need = 4 * sizeof(uint64_t) + 4 * sizeof(double) + n * sizeof(double);
+    const size_t need = 5 * sizeof(uint64_t) + kScalarsPerScenario * (size_t)h->S * sizeof(double) +
+                        n * sizeof(double);
     const uint64_t *hdr = (const uint64_t *)buf;
     if (len != need || hdr[0] != kStateMagic || hdr[1] != (uint64_t)h->nb || hdr[2] != (uint64_t)h->nl ||
-        hdr[3] != (uint64_t)h->ng) {
-        set_err("state blob does not match this grid");
+        hdr[3] != (uint64_t)h->ng || hdr[4] != (uint64_t)h->S) {
+        set_err("state blob does not match this handle");
         return ADMM_ERR_INVALID_ARG;
     }
-    const double *sc = (const double *)(hdr + 4);
-    CK(cudaMemcpyAsync(h->hctrl, h->G.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    h->hctrl->beta = sc[0];
-    h->hctrl->total_iters = (int32_t)sc[1];
-    h->hctrl->beta_used = sc[2];
-    h->hctrl->pending = (int32_t)sc[3];
-    h->hctrl->done = 0;
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
+    const double *sc = (const double *)(hdr + 5);
+    for (int s = 0; s < h->S; ++s) {
+        SCtrl &c = h->hsc[s];
+        c.beta = sc[4 * s];
+        c.total_iters = (int32_t)sc[4 * s + 1];
+        c.beta_used = sc[4 * s + 2];
+        c.pending = (int32_t)sc[4 * s + 3];
+    }
     std::memset(h->hctrl->cls_count, 0, sizeof(h->hctrl->cls_count));   // queue order restarts
-    const double *p = sc + 4;
+    const double *p = sc + kScalarsPerScenario * h->S;
     for (auto &pt : parts) {
         if (pt.n) CK(cudaMemcpyAsync(pt.dev, p, pt.n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         p += pt.n;
     }
+    CK(cudaMemcpyAsync(h->G.sc, h->hsc, sizeof(SCtrl) * h->S, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->G.ctrl, h->hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return ADMM_OK;
@@ -805,10 +1005,10 @@ extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
 extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out)
 {
     if (!h || !ms_out || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
-    SolveParams sp{0.0, h->opts.rho_pq, h->opts.rho_va, iters, 1};
-    begin_kernel<<<1, 32, 0, h->stream>>>(h->G, h->O, sp);
-    int rc = launch_check("begin_kernel");
+    int rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, iters, 1);
     if (rc != ADMM_OK) return rc;
+    run_begin_kernel<<<1, 32, 0, h->stream>>>(h->G, iters);
+    if ((rc = launch_check("run_begin_kernel")) != ADMM_OK) return rc;
     std::vector<cudaEvent_t> ev(2 * (size_t)iters + 1);
     for (auto &e : ev) CK(cudaEventCreate(&e));
     cudaGraphConditionalHandle none = 0;
@@ -816,10 +1016,12 @@ extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms
     for (int it = 0; it < iters; ++it) {
         branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
         CK(cudaEventRecord(ev[2 * it + 1], h->stream));
-        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O, none, 0);
+        bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
+        control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
         CK(cudaEventRecord(ev[2 * it + 2], h->stream));
     }
     flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
+    clear_pending_kernel<<<(h->S + 255) / 256, 256, 0, h->stream>>>(h->G);
     if ((rc = launch_check("profiled iteration")) != ADMM_OK) return rc;
     CK(cudaStreamSynchronize(h->stream));
     double tb = 0.0, tu = 0.0;
