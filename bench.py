@@ -173,6 +173,70 @@ def workload_config(grid, opts, args):
             "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
 
 
+def run_batched(args, admm, stream):
+    """Scenarios of uneven size in one batched handle (one persistent launch
+    per iteration over the flattened component index, per-scenario stopping),
+    autotuned; against a loop of plain one-grid solves on a sample."""
+    import numpy as np
+    import torch
+    from paper_2110_06879_gb300 import synth
+    grids = synth.batch_grids(args.batched, lo=500, hi=20000, seed=args.seed)
+    kw = dict(rho_pq=3e3, rho_va=3e4)
+    b = admm.Solver(grids, stream=stream, **kw)
+    blocks, _ = b.autotune(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.solve(tol=1e-3, max_iter=3000)        # cold start of every scenario
+    dt = time.perf_counter() - t0
+    st, it = b.slot_status()
+    b.close()
+    rng = np.random.default_rng(args.seed)
+    sample = rng.choice(len(grids), min(args.batch_sample, len(grids)), replace=False)
+    tloop = 0.0
+    for k in sample:
+        s = admm.Solver(grids[int(k)], stream=stream, **kw)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.solve(tol=1e-3, max_iter=3000)
+        tloop += time.perf_counter() - t1
+        s.close()
+    return {"scenarios": len(grids), "buses": int(sum(g.nbus for g in grids)),
+            "branches": int(sum(g.nbranch for g in grids)), "seconds": dt,
+            "scenarios_per_s": len(grids) / dt, "converged": int((st == 0).sum()),
+            "iters_p50": int(np.median(it)), "iters_max": int(it.max()),
+            "autotuned_branch_blocks": blocks,
+            "plain_loop_sample": len(sample), "plain_loop_scenarios_per_s": len(sample) / tloop,
+            "speedup_vs_plain_loop": (len(grids) / dt) / (len(sample) / tloop),
+            "tol": 1e-3, "max_iter": 3000, "rho_pq": kw["rho_pq"], "rho_va": kw["rho_va"]}
+
+
+def run_served(args, admm, stream):
+    """Continuous batching over a resident pool (log-uniform 1k-70k buses, one
+    grid pinned at 70k) under Poisson load-snapshot requests, against the same
+    stream served by serial plain solves."""
+    import numpy as np
+    from paper_2110_06879_gb300 import serve, synth
+    rng = np.random.Generator(np.random.PCG64(args.seed + 5))
+    sizes = list(np.exp(rng.uniform(np.log(1000), np.log(70000), args.pool - 1)).astype(int))
+    sizes.append(70000)
+    grids = [synth.sized_grid(int(n), seed=500 + k) for k, n in enumerate(sizes)]
+    srv = serve.Server(grids, mem_budget=args.mem_budget_gb << 30, tick_iters=8, max_iter=500,
+                       stream=stream)
+    warm = srv.warm_up()
+    reqs = serve.poisson_requests(grids, rate=args.rate, duration=args.serve_seconds,
+                                  seed=args.seed + 9)
+    recs, rejected, wall = srv.run(reqs, deadline=2 * args.serve_seconds)
+    srv.solver.close()
+    recs2, wall2 = serve.serial_baseline(grids, reqs, max_iter=500, stream=stream,
+                                         deadline=2 * args.serve_seconds)
+    return {"pool": len(grids), "resident": len(srv.grid_ids), "resident_bytes": srv.bytes,
+            "pool_buses": int(sum(sizes)), "rate_per_s": args.rate,
+            "arrival_seconds": args.serve_seconds, "pool_cold_solve_s": warm,
+            "served": serve.summarize(recs, wall), "rejected": len(rejected),
+            "serial": serve.summarize(recs2, wall2),
+            "tol": 1e-3, "max_iter_per_request": 500, "tick_iters": 8}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -287,6 +351,9 @@ def run_ours(args):
                       "rho_pq": topts["rho_pq"], "rho_va": topts["rho_va"], "tol": 1e-3})
         ts.close()
 
+    batched = run_batched(args, admm, stream) if args.batched > 0 else None
+    served = run_served(args, admm, stream) if args.served else None
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": sum(iter_ms) / len(iter_ms),
@@ -304,6 +371,10 @@ def run_ours(args):
             line["time_to_tol"] = tt
         if track is not None:
             line["tracking"] = track
+        if batched is not None:
+            line["batched"] = batched
+        if served is not None:
+            line["served"] = served
         if args.cpu_baseline and ws >= 1:
             line["cpu_baseline"] = cpu_baseline(grid, opts, args.cpu_seconds)
         print(json.dumps(line))
@@ -327,6 +398,14 @@ def main():
     ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false")
     ap.add_argument("--tol-max-iter", type=int, default=5000)
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="add the batched leg with this many scenarios (256 in the workload)")
+    ap.add_argument("--batch-sample", type=int, default=8)
+    ap.add_argument("--served", action="store_true", help="add the continuous-batching leg")
+    ap.add_argument("--pool", type=int, default=32)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--mem-budget-gb", type=int, default=16)
     ap.add_argument("--track-steps", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 3:

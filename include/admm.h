@@ -279,6 +279,14 @@ int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
                              const double *d_lambda, double beta, int32_t two_level,
                              double *d_z, double *d_y, double *d_norms, void *cuda_stream);
 
+/* Autotuner: times the branch_tron launch for 5 resident-block counts (1/2,
+ * 3/4, 1, 3/2 and 2 blocks of 128 lanes per SM), interleaved, `iters` times
+ * each, and keeps the fastest for later solves (the iteration graph is
+ * rebuilt).  The 5 * iters timed iterations are real warm iterations of every
+ * scenario (the state advances; block counts never change results).
+ * *chosen (may be NULL) receives the block count, *ms_best its mean time. */
+int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best);
+
 const char *admm_status_string(int status);
 /* Text of the last error recorded by any call in this process (thread-local). */
 const char *admm_last_error(void);

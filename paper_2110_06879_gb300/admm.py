@@ -90,6 +90,7 @@ def lib():
             "admm_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
             "admm_set_state": (C.c_int, [vp, vp, C.c_size_t]),
             "admm_profile_iterations": (C.c_int, [vp, i32, vp]),
+            "admm_autotune": (C.c_int, [vp, i32, vp, vp]),
             "admm_dual_update_noalloc": (C.c_int, [C.c_int64, vp, vp, vp, vp, vp, d, i32, vp, vp,
                                                    vp, vp]),
             "admm_status_string": (C.c_char_p, [C.c_int]),
@@ -284,6 +285,12 @@ class Solver:
         out = np.zeros(3)
         _check(lib().admm_profile_iterations(self.h, iters, _ptr(out)), "admm_profile_iterations")
         return dict(branch_ms=out[0], bus_ms=out[1], iter_ms=out[2])
+
+    def autotune(self, iters=3):
+        n = C.c_int32(0)
+        ms = C.c_double(0.0)
+        _check(lib().admm_autotune(self.h, iters, C.byref(n), C.byref(ms)), "admm_autotune")
+        return int(n.value), float(ms.value)
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)

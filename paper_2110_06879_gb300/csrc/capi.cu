@@ -1002,6 +1002,69 @@ extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
     return ADMM_OK;
 }
 
+extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best)
+{
+    if (!h || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 152;
+    cudaGetLastError();
+    const int need = (h->nl + kBranchBlock - 1) / kBranchBlock;
+    int cand[5] = {sms / 2, (3 * sms) / 4, sms, (3 * sms) / 2, 2 * sms};
+    double tot[5] = {0, 0, 0, 0, 0};
+    int rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, 5 * iters, 1);
+    if (rc != ADMM_OK) return rc;
+    run_begin_kernel<<<1, 32, 0, h->stream>>>(h->G, 5 * iters);
+    if ((rc = launch_check("run_begin_kernel")) != ADMM_OK) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaGraphConditionalHandle none = 0;
+    // interleave the candidates so each sees iterations from the same stretch
+    for (int r = 0; r < iters; ++r) {
+        for (int c = 0; c < 5; ++c) {
+            const int nbk = cand[c] < need ? (cand[c] > 0 ? cand[c] : 1) : need;
+            DevGrid G = h->G;
+            G.nblk_branch = nbk;
+            CK(cudaEventRecord(e0, h->stream));
+            branch_tron_kernel<<<nbk, kBranchBlock, 0, h->stream>>>(G, h->O);
+            CK(cudaEventRecord(e1, h->stream));
+            bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
+            control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
+            if ((rc = launch_check("autotune iteration")) != ADMM_OK) return rc;
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            tot[c] += ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
+    clear_pending_kernel<<<(h->S + 255) / 256, 256, 0, h->stream>>>(h->G);
+    if ((rc = launch_check("flush_lambda_kernel")) != ADMM_OK) return rc;
+    int best = 0;
+    for (int c = 1; c < 5; ++c)
+        if (tot[c] < tot[best]) best = c;
+    const int nbk = cand[best] < need ? (cand[best] > 0 ? cand[best] : 1) : need;
+    h->nblk_branch = nbk;
+    h->G.nblk_branch = nbk;
+    h->opts.branch_blocks = nbk;
+    if (h->opts.use_graph) {
+        destroy_graph(h);
+        if (build_graph(h) != ADMM_OK) {
+            destroy_graph(h);
+            cudaGetLastError();
+            h->opts.use_graph = 0;
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (chosen) *chosen = nbk;
+    if (ms_best) *ms_best = tot[best] / iters;
+    return ADMM_OK;
+}
+
 extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out)
 {
     if (!h || !ms_out || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }

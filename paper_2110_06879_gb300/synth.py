@@ -262,3 +262,17 @@ def ar1_loads(grid: Grid, steps: int, seed: int, phi: float = 0.9, sigma: float 
         pds.append(grid.pd * (1.0 + a))
         qds.append(grid.qd * (1.0 + a))
     return np.array(pds), np.array(qds)
+
+
+def batch_grids(n: int, lo: int = 500, hi: int = 20000, seed: int = 0, load_noise: float = 0.02):
+    """`n` independent grids with bus counts log-uniform in [lo, hi] (branches
+    and generators in the ACTIVSg70k ratios of Table 1), each with its own
+    seeded load perturbation pd (1 + load_noise N(0,1)) (qd likewise)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(int)
+    out = []
+    for k, nb in enumerate(sizes):
+        g = sized_grid(int(nb), seed=seed * 100003 + k)
+        r = np.random.Generator(np.random.PCG64(seed * 7919 + k)).standard_normal(g.nbus)
+        out.append(g.with_loads(g.pd * (1.0 + load_noise * r), g.qd * (1.0 + load_noise * r)))
+    return out
