@@ -280,11 +280,14 @@ int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
                              double *d_z, double *d_y, double *d_norms, void *cuda_stream);
 
 /* Autotuner: times the branch_tron launch for 5 resident-block counts (1/2,
- * 3/4, 1, 3/2 and 2 blocks of 128 lanes per SM), interleaved, `iters` times
- * each, and keeps the fastest for later solves (the iteration graph is
- * rebuilt).  The 5 * iters timed iterations are real warm iterations of every
- * scenario (the state advances; block counts never change results).
- * *chosen (may be NULL) receives the block count, *ms_best its mean time. */
+ * 3/4, 1, 3/2 and 2 blocks of 128 lanes per SM) and keeps the fastest for
+ * later solves (the iteration graph is rebuilt).  Every candidate replays the
+ * same `iters` warm iterations of every scenario from a device copy of the
+ * current state, twice (forward and reverse candidate order); afterwards the
+ * state is put back, so the tuner changes no result and no iteration count.
+ * It allocates one temporary device buffer the size of the iteration state
+ * (ADMM_ERR_OOM if that fails).  *chosen (may be NULL) receives the block
+ * count, *ms_best the fastest candidate's mean branch_tron time. */
 int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best);
 
 const char *admm_status_string(int status);

@@ -53,7 +53,8 @@ class OraOptions(C.Structure):
 class OraBranchProb(C.Structure):
     _fields_ = [("Y", C.c_double * 8), ("lo", C.c_double * 6), ("hi", C.c_double * 6),
                 ("xbar", C.c_double * 8), ("z", C.c_double * 8), ("y", C.c_double * 8),
-                ("rho", C.c_double * 8), ("lt", C.c_double * 2), ("rt", C.c_double)]
+                ("rho", C.c_double * 8), ("lt", C.c_double * 2), ("rt", C.c_double),
+                ("alpha", C.c_double)]
 
 
 class OraStats(C.Structure):
@@ -239,6 +240,7 @@ def branch_prob(Y, lo, hi, xbar, z, y, rho, lt, rt) -> OraBranchProb:
         for i, v in enumerate(val):
             arr[i] = float(v)
     p.rt = float(rt)
+    p.alpha = 1.0
     return p
 
 

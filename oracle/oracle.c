@@ -409,10 +409,12 @@ static void subspace(const double *x, const double *g, const double *H, const do
  * start) or on a step with ||s||_inf <= xtol * max(1, ||x||_inf); status 1
  * after tron_max_iter iterations; status 2 when the radius falls below
  * 1e-14 max(1, ||x||_inf) or the model predicts no decrease.
- * The initial radius is ||P(x0 - g0) - x0||_2 and the first Cauchy alpha is 1.
+ * The initial radius is ||P(x0 - g0) - x0||_2.  The Cauchy search starts from
+ * the alpha the branch's previous TRON call ended with (bp->alpha; 1 for the
+ * first call) and hands its last alpha back in bp->alpha.
  * A step whose predicted decrease is at most ftol * max(1, |f|) lies below
  * the rounding level of f; the model is trusted for it (ratio taken as 1). */
-int ora_tron(const ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st)
+int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st)
 {
     const double *lo = bp->lo, *hi = bp->hi;
     double f, g[NV], H[NV * NV];
@@ -425,7 +427,7 @@ int ora_tron(const ora_branch_prob *bp, double *x, const ora_options *o, ora_sta
     double sp[NV];
     pstep(x, g, 1.0, lo, hi, sp);
     double delta = nrm2(sp);
-    double alpha = 1.0;
+    double alpha = bp->alpha > 0.0 ? bp->alpha : 1.0;
     int status = 1;
     for (int k = 0; k < o->tron_max_iter; ++k) {
         if (pgnorm(x, g, lo, hi) <= gtol) { status = 0; break; }
@@ -467,6 +469,7 @@ int ora_tron(const ora_branch_prob *bp, double *x, const ora_options *o, ora_sta
         if (delta <= 1e-14 * (xn > 1.0 ? xn : 1.0)) { status = 2; break; }
     }
     if (status == 1) st->tron_maxiter_hits++;
+    bp->alpha = alpha;
     return status;
 }
 
@@ -474,7 +477,8 @@ int ora_tron(const ora_branch_prob *bp, double *x, const ora_options *o, ora_sta
  * (Section II-C; the schedule is this implementation's reading): rho-tilde
  * starts at al_rho0, each pass solves eq. branch by TRON, then
  * lt += rt h; stop when max|h| <= al_tol, else rt *= al_rho_factor (capped)
- * when max|h| did not fall below al_decay times its previous value. */
+ * when max|h| did not fall below al_decay times its previous value.  The
+ * Cauchy alpha of each TRON call carries into the next one (bp->alpha). */
 void ora_branch_solve(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st)
 {
     double hprev = INFINITY;
@@ -527,6 +531,7 @@ struct ora {
     int *row, *col;
     /* state */
     double *u, *xbar, *z, *y, *lam, *rho, *bx, *lt, *bus;
+    double *balpha;             /* per branch: Cauchy alpha of its last TRON call */
     double beta, tol_in, zprev;
     int outer, inner;
     /* results */
@@ -601,6 +606,7 @@ ora *ora_create(const ora_grid *g, const ora_options *o)
     p->u = dup_d(NULL, m); p->xbar = dup_d(NULL, m); p->z = dup_d(NULL, m);
     p->y = dup_d(NULL, m); p->lam = dup_d(NULL, m); p->rho = dup_d(NULL, m);
     p->bx = dup_d(NULL, 6 * p->nl); p->lt = dup_d(NULL, 2 * p->nl);
+    p->balpha = dup_d(NULL, p->nl);
     p->bus = dup_d(NULL, 2 * p->nb);
     p->hist = dup_d(NULL, 4 * HIST_CAP);
     /* penalties: rho_pq for generator and flow couplings, rho_va for w, theta */
@@ -617,7 +623,7 @@ void ora_destroy(ora *p)
     free(p->pbase_lo); free(p->pbase_hi);
     double *d[] = {p->pd, p->qd, p->gs, p->bs, p->vmin, p->vmax, p->rate, p->Y, p->pmin,
                    p->pmax, p->qmin, p->qmax, p->c2, p->c1, p->c0, p->u, p->xbar, p->z,
-                   p->y, p->lam, p->rho, p->bx, p->lt, p->bus, p->hist};
+                   p->y, p->lam, p->rho, p->bx, p->lt, p->bus, p->hist, p->balpha};
     for (unsigned i = 0; i < sizeof(d) / sizeof(d[0]); ++i) free(d[i]);
     free(p->fb); free(p->tb); free(p->gb); free(p->row); free(p->col);
     free(p);
@@ -670,6 +676,7 @@ void ora_cold_start(ora *p)
         x[4] = proj1(-(fl[0] * fl[0] + fl[1] * fl[1]), slo, 0.0);
         x[5] = proj1(-(fl[2] * fl[2] + fl[3] * fl[3]), slo, 0.0);
         p->lt[2 * l] = 0.0; p->lt[2 * l + 1] = 0.0;
+        p->balpha[l] = 1.0;
         for (int k = 0; k < 4; ++k) p->u[cb(p, l, k)] = fl[k];
         p->u[cb(p, l, 4)] = x[0] * x[0];
         p->u[cb(p, l, 5)] = 0.0;
@@ -743,9 +750,11 @@ static void update_branches(ora *p, int l0, int l1)
         }
         bp.lt[0] = p->lt[2 * l]; bp.lt[1] = p->lt[2 * l + 1];
         bp.rt = p->o.al_rho0 > 0.0 ? p->o.al_rho0 : p->o.rho_pq;
+        bp.alpha = p->balpha[l];
         double *x = &p->bx[6 * l];
         ora_branch_solve(&bp, x, &p->o, &p->st);
         p->lt[2 * l] = bp.lt[0]; p->lt[2 * l + 1] = bp.lt[1];
+        p->balpha[l] = bp.alpha;
         double fl[4];
         ora_branch_flows(bp.Y, x, fl);
         for (int k = 0; k < 4; ++k) p->u[cb(p, l, k)] = fl[k];

@@ -55,6 +55,8 @@ typedef struct {
     double xbar[8], z[8], y[8], rho[8];   /* coupling data, order as above      */
     double lt[2];           /* lambda-tilde of the two line-limit equalities     */
     double rt;              /* rho-tilde                                         */
+    double alpha;           /* Cauchy step length carried into the next TRON
+                               call and back out of it (<= 0: start at 1)       */
 } ora_branch_prob;
 
 /* counters of one branch solve (or summed over many) */
@@ -86,7 +88,7 @@ void ora_finalize(const ora *p, double *pg, double *qg, double *vm, double *va,
 void ora_admittance(double r, double x, double b, double tap, double shift, double *Y8);
 void ora_branch_fgh(const ora_branch_prob *bp, const double *x, double *f, double *g, double *H);
 void ora_branch_flows(const double *Y8, const double *x, double *flows4);
-int ora_tron(const ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st);
+int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st);
 void ora_branch_solve(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st);
 double ora_gen_solve(double cost2, double cost1, double rho, double xbar, double z, double y,
                      double lo, double hi);

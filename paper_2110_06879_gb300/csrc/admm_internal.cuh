@@ -4,7 +4,8 @@
 // generators, nb buses, ns = 2 nl + ng incidence slots in CSR order):
 //   branch params  Y[8][nl] (g_ii b_ii g_ij b_ij g_ji b_ji g_jj b_jj),
 //                  lim[5][nl] (vmin_i, vmax_i, vmin_j, vmax_j, s lower bound)
-//   branch state   bx[6][nl] (v_i v_j th_i th_j s_ij s_ji), blt[2][nl] (lambda-tilde)
+//   branch state   bx[6][nl] (v_i v_j th_i th_j s_ij s_ji), blt[2][nl] (lambda-tilde),
+//                  balpha[nl] (Cauchy step length of the last TRON call)
 //   branch I/O     bt[8][nl] targets xbar - z - y/rho written by the bus kernel,
 //                  bu[8][nl] component-side coupling values written by branch_tron
 //   generators     gc[3][ng] (c2' c1' c0 per-unit costs), glim[4][ng], gu[2][ng]
@@ -44,6 +45,9 @@ struct SCtrl {
     unsigned int fin_counter;      // last-block ticket of finalize for this scenario
 };
 
+// scheduling classes of branch_tron by loop trips: >= 64, 48, 32, 24, 16, 8, 4, < 4
+constexpr int kClasses = 8;
+
 // Whole-handle state of one run of the iteration loop.
 struct Ctrl {
     int32_t run_iter, run_max, n_live, done;
@@ -51,8 +55,8 @@ struct Ctrl {
     unsigned int branch_next;      // work queue head of branch_tron (reset every iteration)
     unsigned int pad1;
     // longest-first scheduling of branch_tron: branches filed by the loop trips
-    // they needed, three classes, double-buffered by iteration parity
-    unsigned int cls_count[2][4];
+    // they needed (kClasses classes), double-buffered by iteration parity
+    unsigned int cls_count[2][kClasses];
     unsigned long long stats[kNumStats];
 };
 
@@ -78,6 +82,7 @@ struct DevGrid {
     // branches
     const int32_t *f_bus, *t_bus;
     double *Y, *lim, *bx, *blt, *bt, *bu;
+    double *balpha;
     const double *raw;             // r x b tap shift rate [6][nl] for the admittance kernel
     // generators
     const int32_t *gen_bus;
@@ -89,7 +94,7 @@ struct DevGrid {
     // slots
     double *sx, *sz, *sy, *sl;
     // scratch and control
-    int32_t *cls_list;             // [2][3][nl] branch ids per (parity, class)
+    int32_t *cls_list;             // [2][kClasses][nl] branch ids per (parity, class)
     double *partials;              // [nblk_bus][8]
     double *fin_partials;          // [nblk_fin][2] (one scenario at a time)
     double *hist;                  // [kHistCap][4], scenario 0 only

@@ -281,7 +281,8 @@ __device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, cons
 // another.  Inactive lanes compute on stale registers only (no memory access).
 
 // Generalised Cauchy step along the projected-gradient path: from the carried
-// alpha, backtrack by 0.1 while the sufficient-decrease / radius test fails, or
+// alpha (the previous TRON iteration's, or the branch's previous TRON call's
+// at the first iteration), backtrack by 0.1 while the sufficient-decrease / radius test fails, or
 // extrapolate by 10 while it holds and the path still moves.  Until the path
 // meets a bound, s(alpha) = -alpha g_P (g_P: g without the components pinned at
 // a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
@@ -352,14 +353,15 @@ __device__ __forceinline__ double boundary_tau(const double *a, const double *pv
 
 // one Cholesky pass of D^-1 A D^-1 + sigma I on the free block (identity on
 // fixed variables); the diagonal of L keeps the reciprocal pivots.  Lanes
-// with keep == true leave L unchanged.
+// with keep == true leave L unchanged.  kPlain: D = I and sigma = 0.
+template <bool kPlain>
 __device__ __forceinline__ bool chol_pass(const double *H, const bool *fr, const double *dinv,
                                           double sigma, bool keep, double *L)
 {
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double dd = fr[j] ? H[P(j, j)] * dinv[j] * dinv[j] + sigma : 1.0;
+        double dd = fr[j] ? (kPlain ? H[P(j, j)] : H[P(j, j)] * dinv[j] * dinv[j] + sigma) : 1.0;
 #pragma unroll
         for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
         ok = ok && dpos(dd);
@@ -367,7 +369,7 @@ __device__ __forceinline__ bool chol_pass(const double *H, const bool *fr, const
         L[P(j, j)] = keep ? L[P(j, j)] : linv;
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            double v = (fr[i] && fr[j]) ? H[P(i, j)] * dinv[i] * dinv[j] : 0.0;
+            double v = (fr[i] && fr[j]) ? (kPlain ? H[P(i, j)] : H[P(i, j)] * dinv[i] * dinv[j]) : 0.0;
 #pragma unroll
             for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
             L[P(i, j)] = keep ? L[P(i, j)] : v * linv;
@@ -386,7 +388,7 @@ __device__ __forceinline__ void precond_factor(bool on, const double *H, const b
 {
 #pragma unroll
     for (int i = 0; i < 6; ++i) dinv[i] = 1.0;
-    const bool plain = chol_pass(H, fr, dinv, 0.0, false, L);
+    const bool plain = chol_pass<true>(H, fr, dinv, 0.0, false, L);
     bool need = on && !plain;
     if (!__any_sync(kFull, need)) return;
     bool pos = true;
@@ -402,7 +404,7 @@ __device__ __forceinline__ void precond_factor(bool on, const double *H, const b
     double sigma = pos ? 0.0 : 1e-3;
     for (int tries = 0; tries < kCholTries; ++tries) {
         if (!__any_sync(kFull, need)) break;
-        const bool ok = chol_pass(H, fr, dinv, sigma, !need, L);
+        const bool ok = chol_pass<false>(H, fr, dinv, sigma, !need, L);
         need = need && !ok;
         sigma = dmaxi(sigma * 2.0, 1e-3);
     }
@@ -556,13 +558,21 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long *dst, int v)
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
+// Scheduling class of a branch that took `trips` loop trips (0 = hardest).
+__device__ __forceinline__ int trip_class(int trips)
+{
+    return trips >= 64 ? 0 : trips >= 48 ? 1 : trips >= 32 ? 2 : trips >= 24 ? 3
+         : trips >= 16 ? 4 : trips >= 8 ? 5 : trips >= 4 ? 6 : 7;
+}
+
 // File the branches some lanes finished (filed >= 0) into the class lists of
 // the next iteration (warp-collective; one atomic per class and warp).
 __device__ __forceinline__ void file_branches(Ctrl *ctrl, int32_t *lnxt, int nl, int nxt, int lane,
                                               int filed, int fcls)
 {
+    if (!__any_sync(kFull, filed >= 0)) return;
 #pragma unroll
-    for (int cl = 0; cl < 3; ++cl) {
+    for (int cl = 0; cl < kClasses; ++cl) {
         const unsigned m = __ballot_sync(kFull, filed >= 0 && fcls == cl);
         if (m) {
             const int leader = __ffs(m) - 1;
@@ -583,8 +593,9 @@ __global__ void __launch_bounds__(kBranchBlock, kBranchBlocksPerSM)
 branch_tron_kernel(DevGrid G, DevOpts O)
 {
     __shared__ double sh[16 * kBranchBlock];   // per lane: Y[8], t[8], stride kBranchBlock
+    __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
     Ctrl *ctrl = G.ctrl;
-    if (ctrl->done) return;
+    if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
     const int lane = threadIdx.x & 31;
     const double *sY = sh + threadIdx.x;
@@ -594,11 +605,15 @@ branch_tron_kernel(DevGrid G, DevOpts O)
 
     // queue order: the classes filed by the previous iteration, hardest first
     const int cur = ctrl->total_iters & 1, nxt = cur ^ 1;
-    const unsigned n0 = ctrl->cls_count[cur][0], n1 = ctrl->cls_count[cur][1];
-    const unsigned n2 = ctrl->cls_count[cur][2];
-    const bool ordered = n0 + n1 + n2 == (unsigned)nl;
-    const int32_t *lcur = G.cls_list + (size_t)cur * 3 * nl;
-    int32_t *lnxt = G.cls_list + (size_t)nxt * 3 * nl;
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        cstart[0] = 0;
+        for (int k = 0; k < kClasses; ++k) cstart[k + 1] = (acc += ctrl->cls_count[cur][k]);
+    }
+    __syncthreads();
+    const bool ordered = cstart[kClasses] == (unsigned)nl;
+    const int32_t *lcur = G.cls_list + (size_t)cur * kClasses * nl;
+    int32_t *lnxt = G.cls_list + (size_t)nxt * kClasses * nl;
 
     int b = -1, state = LS_IDLE, apass = 0, k = 0, trips = 0;
     bool exhausted = false;
@@ -669,6 +684,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 for (int i = 0; i < 6; ++i) G.bx[i * nl + b] = x[i];
                 G.blt[b] = lt0;
                 G.blt[nl + b] = lt1;
+                G.balpha[b] = alpha;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) G.bu[i * nl + b] = F[i];
                 G.bu[4 * nl + b] = x[0] * x[0];
@@ -676,7 +692,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 G.bu[6 * nl + b] = x[1] * x[1];
                 G.bu[7 * nl + b] = x[3];
                 filed = b;
-                fcls = trips >= 24 ? 0 : trips >= 8 ? 1 : 2;
+                fcls = trip_class(trips);
                 b = -1;
                 state = LS_IDLE;
             } else {
@@ -698,10 +714,12 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             if (state == LS_IDLE && !exhausted) {
                 const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
                 if (idx < (unsigned)nl) {
-                    const int bb = !ordered ? (int)idx
-                        : idx < n0 ? lcur[idx]
-                        : idx < n0 + n1 ? lcur[nl + (idx - n0)]
-                                        : lcur[2 * (size_t)nl + (idx - n0 - n1)];
+                    int bb = (int)idx;
+                    if (ordered) {
+                        int cl = 0;
+                        for (int q = 1; q < kClasses; ++q) cl = idx >= cstart[q] ? q : cl;
+                        bb = lcur[(size_t)cl * nl + (idx - cstart[cl])];
+                    }
                     const SCtrl *sc = G.sc + G.br_scen[bb];
                     if (!sc->active || sc->done) {
                         skip = bb;
@@ -727,6 +745,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                         for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
                         lt0 = G.blt[b];
                         lt1 = G.blt[nl + b];
+                        alpha = G.balpha[b];
                         rt = rt0;
                         hprev = __longlong_as_double(0x7ff0000000000000LL);
                         apass = 0;
@@ -736,7 +755,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                     exhausted = true;
                 }
             }
-            file_branches(ctrl, lnxt, nl, nxt, lane, skip, 2);
+            file_branches(ctrl, lnxt, nl, nxt, lane, skip, kClasses - 1);
         }
         // done when every lane is idle and the queue is drained
         if (!__any_sync(kFull, state != LS_IDLE || !exhausted)) break;
@@ -769,7 +788,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             double sp[6];
             pstep(B, x, g, 1.0, sp);
             delta = sqrt(dot6(sp, sp));
-            alpha = 1.0;
+            alpha = dpos(alpha) ? alpha : 1.0;   // carried from the previous call
             k = 0;
             state = LS_ITER;
         } else if (state == LS_REEVAL) {

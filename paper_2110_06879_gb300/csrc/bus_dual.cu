@@ -124,6 +124,7 @@ __global__ void cold_start_kernel(DevGrid G, Range R, double beta_init)
         for (int k = 0; k < 6; ++k) G.bx[k * nl + l] = x[k];
         G.blt[l] = 0.0;
         G.blt[nl + l] = 0.0;
+        G.balpha[l] = 1.0;
         double u[8] = {fl[0], fl[1], fl[2], fl[3], vi * vi, 0.0, vj * vj, 0.0};
         for (int k = 0; k < 8; ++k) {
             G.bu[k * nl + l] = u[k];
@@ -231,6 +232,9 @@ bus_dual_kernel(DevGrid G, DevOpts O)
     const int i = G.bus_off[sid] + (blockIdx.x - blk0) * blockDim.x + threadIdx.x;
     const int i_end = G.bus_off[sid + 1];
     const double rpq = c->rho_pq, rva = c->rho_va, beta = c->beta;
+    // reciprocals once per block: a division costs about ten FP64 instructions
+    const double irpq = 1.0 / rpq, irva = 1.0 / rva;
+    const double izpq = 1.0 / (beta + rpq), izva = 1.0 / (beta + rva);
     const bool pending = c->pending != 0;
     const double bused = c->beta_used, lmax = O.lambda_max;
     const bool two = O.two_level != 0;
@@ -251,10 +255,10 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                 const double uW = G.bu[(end ? 6 : 4) * nl + l], uT = G.bu[(end ? 7 : 5) * nl + l];
                 const double zW = G.sz[2 * ns + k], zT = G.sz[3 * ns + k];
                 const double yW = G.sy[2 * ns + k], yT = G.sy[3 * ns + k];
-                const double tP = uP + zP + yP / rpq, tQ = uQ + zQ + yQ / rpq;
-                const double tW = uW + zW + yW / rva, tT = uT + zT + yT / rva;
-                M00 += 1.0 / rpq;
-                M11 += 1.0 / rpq;
+                const double tP = uP + zP + yP * irpq, tQ = uQ + zQ + yQ * irpq;
+                const double tW = uW + zW + yW * irva, tT = uT + zT + yT * irva;
+                M00 += irpq;
+                M11 += irpq;
                 rP -= tP;
                 rQ -= tQ;
                 qw += rva; cw += rva * tW;
@@ -264,30 +268,32 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                 // eq. qp-bound: Q = 2 s_o c2' + rho, c = rho (xbar - z) - y - s_o c1'
                 const double xP = G.sx[k], xQ = G.sx[ns + k];
                 double pg = (rpq * (xP - zP) - yP - so * G.gc[ng + g]) / (2.0 * so * G.gc[g] + rpq);
-                double qg = (rpq * (xQ - zQ) - yQ) / rpq;
+                double qg = (rpq * (xQ - zQ) - yQ) * irpq;
                 pg = clampd(pg, G.glim[0 * ng + g], G.glim[1 * ng + g]);
                 qg = clampd(qg, G.glim[2 * ng + g], G.glim[3 * ng + g]);
                 G.gu[g] = pg;
                 G.gu[ng + g] = qg;
-                const double tP = pg + zP + yP / rpq, tQ = qg + zQ + yQ / rpq;
-                M00 += 1.0 / rpq;
-                M11 += 1.0 / rpq;
+                const double tP = pg + zP + yP * irpq, tQ = qg + zQ + yQ * irpq;
+                M00 += irpq;
+                M11 += irpq;
                 rP += tP;
                 rQ += tQ;
             }
         }
         // eq. qp-bus: pooled w (A column (-gs, bs)), then the 2x2 solve
         const double gs = G.bus[2 * nb + i], bs = G.bus[3 * nb + i];
-        const double tw = cw / qw;
-        M00 += gs * gs / qw;
-        M11 += bs * bs / qw;
-        const double M01 = -gs * bs / qw;
+        const double iqw = 1.0 / qw;
+        const double tw = cw * iqw;
+        M00 += gs * gs * iqw;
+        M11 += bs * bs * iqw;
+        const double M01 = -gs * bs * iqw;
         rP += -gs * tw - G.bus[i];
         rQ += bs * tw - G.bus[nb + i];
         const double det = M00 * M11 - M01 * M01;
-        const double mu0 = (M11 * rP - M01 * rQ) / det;
-        const double mu1 = (M00 * rQ - M01 * rP) / det;
-        const double w = (cw + gs * mu0 - bs * mu1) / qw;
+        const double idet = 1.0 / det;
+        const double mu0 = (M11 * rP - M01 * rQ) * idet;
+        const double mu1 = (M00 * rQ - M01 * rP) * idet;
+        const double w = (cw + gs * mu0 - bs * mu1) * iqw;
         const double th = (i == c->ref) ? 0.0 : ct / qt;
         const double dw = w - G.bw[i], dth = th - G.bth[i];
         G.bw[i] = w;
@@ -298,7 +304,7 @@ bus_dual_kernel(DevGrid G, DevOpts O)
             const bool isb = e < 2 * nl;
             const int nc = isb ? 4 : 2;
             const int l = e >> 1, end = e & 1;
-            double u[4], rho[4];
+            double u[4], rho[4], irho[4], iz[4];
             if (isb) {
                 u[0] = G.bu[(end ? 2 : 0) * nl + l];
                 u[1] = G.bu[(end ? 3 : 1) * nl + l];
@@ -311,6 +317,10 @@ bus_dual_kernel(DevGrid G, DevOpts O)
             }
             rho[0] = rho[1] = rpq;
             rho[2] = rho[3] = rva;
+            irho[0] = irho[1] = irpq;
+            irho[2] = irho[3] = irva;
+            iz[0] = iz[1] = izpq;
+            iz[2] = iz[3] = izva;
             const double sgn = isb ? 1.0 : -1.0;   // A = -1 for flow copies, +1 for generators
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -318,8 +328,8 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                 const double zc = G.sz[c * ns + k], yc = G.sy[c * ns + k];
                 double xb, dual;
                 if (c < 2) {
-                    const double tc = u[c] + zc + yc / rho[c];
-                    xb = tc + sgn * (c == 0 ? mu0 : mu1) / rho[c];
+                    const double tc = u[c] + zc + yc * irho[c];
+                    xb = tc + sgn * (c == 0 ? mu0 : mu1) * irho[c];
                     dual = rho[c] * (xb - G.sx[c * ns + k]);
                     G.sx[c * ns + k] = xb;
                 } else {
@@ -332,7 +342,7 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                     G.sl[c * ns + k] = lc;
                 }
                 const double r0c = u[c] - xb;
-                const double zn = two ? -(lc + yc + rho[c] * r0c) / (beta + rho[c]) : 0.0;
+                const double zn = two ? -(lc + yc + rho[c] * r0c) * iz[c] : 0.0;
                 const double yn = yc + rho[c] * (r0c + zn);
                 G.sz[c * ns + k] = zn;
                 G.sy[c * ns + k] = yn;
@@ -346,7 +356,7 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                 if (isb) {
                     // component index in bt: from end {0,1,4,5}, to end {2,3,6,7}
                     const int comp = (c < 2 ? c : c + 2) + (end ? 2 : 0);
-                    G.bt[comp * nl + l] = xb - zn - yn / rho[c];
+                    G.bt[comp * nl + l] = xb - zn - yn * irho[c];
                 }
             }
         }
@@ -440,7 +450,7 @@ __global__ void control_kernel(DevGrid G, cudaGraphConditionalHandle cond, int32
         // the branch lists filled by this iteration become the next queue order;
         // the ones it consumed are emptied to be filled next
         const int nxt = (c->total_iters + 1) & 1;
-        for (int r = 0; r < 4; ++r) c->cls_count[nxt][r] = 0u;
+        for (int r = 0; r < kClasses; ++r) c->cls_count[nxt][r] = 0u;
         stop = (c->n_live <= 0 || c->run_iter >= c->run_max) ? 1 : 0;
         c->done = stop;
     }

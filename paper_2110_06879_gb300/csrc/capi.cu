@@ -40,7 +40,7 @@ void set_err(const char *fmt, ...)
         }                                                                            \
     } while (0)
 
-constexpr uint64_t kStateMagic = 0x41444d4d53543031ull;   // "ADMMST01"
+constexpr uint64_t kStateMagic = 0x41444d4d53543032ull;   // "ADMMST02"
 
 }  // namespace
 
@@ -439,6 +439,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     size_t o_bx = cv.take<double>(6 * (size_t)nl), o_blt = cv.take<double>(2 * (size_t)nl);
     size_t o_bt = cv.take<double>(8 * (size_t)nl), o_bu = cv.take<double>(8 * (size_t)nl);
     size_t o_raw = cv.take<double>(6 * (size_t)nl);
+    size_t o_balpha = cv.take<double>(nl);
     size_t o_gb = cv.take<int32_t>(ng > 0 ? ng : 1);
     size_t o_gc = cv.take<double>(3 * (size_t)ng + 1), o_glim = cv.take<double>(4 * (size_t)ng + 1);
     size_t o_gu = cv.take<double>(2 * (size_t)ng + 1);
@@ -447,7 +448,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     size_t o_rp = cv.take<int32_t>(nb + 1), o_col = cv.take<int32_t>(ns);
     size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
     size_t o_sy = cv.take<double>(4 * (size_t)ns), o_sl = cv.take<double>(4 * (size_t)ns);
-    size_t o_cls = cv.take<int32_t>(6 * (size_t)nl);
+    size_t o_cls = cv.take<int32_t>(2 * (size_t)kClasses * nl);
     size_t o_part = cv.take<double>(8 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
     size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
     size_t o_ctrl = cv.take<Ctrl>(1);
@@ -484,6 +485,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     G.bx = (double *)(base + o_bx); G.blt = (double *)(base + o_blt);
     G.bt = (double *)(base + o_bt); G.bu = (double *)(base + o_bu);
     G.raw = (double *)(base + o_raw);
+    G.balpha = (double *)(base + o_balpha);
     G.gen_bus = (int32_t *)(base + o_gb);
     G.gc = (double *)(base + o_gc); G.glim = (double *)(base + o_glim); G.gu = (double *)(base + o_gu);
     G.gbase = (double *)(base + o_gbase);
@@ -926,7 +928,7 @@ std::vector<StatePart> state_parts(admm_handle *h)
     const size_t nl = h->nl, ng = h->ng, nb = h->nb, ns = h->ns;
     return {{h->G.bx, 6 * nl}, {h->G.blt, 2 * nl}, {h->G.bt, 8 * nl}, {h->G.bu, 8 * nl},
             {h->G.gu, 2 * ng}, {h->G.bw, nb},      {h->G.bth, nb},    {h->G.sx, 2 * ns},
-            {h->G.sz, 4 * ns}, {h->G.sy, 4 * ns},  {h->G.sl, 4 * ns}};
+            {h->G.sz, 4 * ns}, {h->G.sy, 4 * ns},  {h->G.sl, 4 * ns}, {h->G.balpha, nl}};
 }
 
 constexpr int kScalarsPerScenario = 4;   // beta, total iterations, beta_used, pending
@@ -1002,6 +1004,34 @@ extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
     return ADMM_OK;
 }
 
+namespace {
+
+// every device region an iteration writes and a later iteration reads: the
+// state arrays, the scheduling class lists and the control blocks
+std::vector<std::pair<void *, size_t>> replay_parts(admm_handle *h)
+{
+    std::vector<std::pair<void *, size_t>> out;
+    for (auto &p : state_parts(h)) out.push_back({p.dev, p.n * sizeof(double)});
+    out.push_back({h->G.cls_list, 2 * (size_t)kClasses * h->nl * sizeof(int32_t)});
+    out.push_back({h->G.ctrl, sizeof(Ctrl)});
+    out.push_back({h->G.sc, (size_t)h->S * sizeof(SCtrl)});
+    return out;
+}
+
+int replay_copy(admm_handle *h, char *snap, bool save)
+{
+    size_t off = 0;
+    for (auto &p : replay_parts(h)) {
+        if (p.second)
+            CK(cudaMemcpyAsync(save ? (void *)(snap + off) : p.first, save ? p.first : (void *)(snap + off),
+                               p.second, cudaMemcpyDeviceToDevice, h->stream));
+        off += (p.second + 255) & ~(size_t)255;
+    }
+    return ADMM_OK;
+}
+
+}  // namespace
+
 extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best)
 {
     if (!h || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
@@ -1011,41 +1041,60 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, dou
         sms = 152;
     cudaGetLastError();
     const int need = (h->nl + kBranchBlock - 1) / kBranchBlock;
-    int cand[5] = {sms / 2, (3 * sms) / 4, sms, (3 * sms) / 2, 2 * sms};
-    double tot[5] = {0, 0, 0, 0, 0};
-    int rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, 5 * iters, 1);
-    if (rc != ADMM_OK) return rc;
-    run_begin_kernel<<<1, 32, 0, h->stream>>>(h->G, 5 * iters);
-    if ((rc = launch_check("run_begin_kernel")) != ADMM_OK) return rc;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    constexpr int kCand = 5;
+    const int cand[kCand] = {sms / 2, (3 * sms) / 4, sms, (3 * sms) / 2, 2 * sms};
+    double tot[kCand] = {0, 0, 0, 0, 0};
+    size_t bytes = 0;
+    for (auto &p : replay_parts(h)) bytes += (p.second + 255) & ~(size_t)255;
+    char *snap = nullptr;
+    CK(cudaMalloc(&snap, bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = replay_copy(h, snap, true);
+    if (rc == ADMM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        set_err("cudaEventCreate failed");
+        rc = ADMM_ERR_CUDA;
+    }
     cudaGraphConditionalHandle none = 0;
-    // interleave the candidates so each sees iterations from the same stretch
-    for (int r = 0; r < iters; ++r) {
-        for (int c = 0; c < 5; ++c) {
+    // two passes, the second in reverse order; every candidate replays the
+    // same `iters` iterations from the same saved state
+    for (int pass = 0; pass < 2 && rc == ADMM_OK; ++pass) {
+        for (int k = 0; k < kCand && rc == ADMM_OK; ++k) {
+            const int c = pass == 0 ? k : kCand - 1 - k;
             const int nbk = cand[c] < need ? (cand[c] > 0 ? cand[c] : 1) : need;
             DevGrid G = h->G;
             G.nblk_branch = nbk;
-            CK(cudaEventRecord(e0, h->stream));
-            branch_tron_kernel<<<nbk, kBranchBlock, 0, h->stream>>>(G, h->O);
-            CK(cudaEventRecord(e1, h->stream));
-            bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
-            control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
-            if ((rc = launch_check("autotune iteration")) != ADMM_OK) return rc;
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            tot[c] += ms;
+            if ((rc = replay_copy(h, snap, false)) != ADMM_OK) break;
+            if ((rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, iters, 1)) != ADMM_OK) break;
+            run_begin_kernel<<<1, 32, 0, h->stream>>>(h->G, iters);
+            for (int it = 0; it < iters && rc == ADMM_OK; ++it) {
+                float ms = 0.f;
+                if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = ADMM_ERR_CUDA; break; }
+                branch_tron_kernel<<<nbk, kBranchBlock, 0, h->stream>>>(G, h->O);
+                if (cudaEventRecord(e1, h->stream) != cudaSuccess) { rc = ADMM_ERR_CUDA; break; }
+                bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
+                control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
+                if ((rc = launch_check("autotune iteration")) != ADMM_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    set_err("autotune timing failed");
+                    rc = ADMM_ERR_CUDA;
+                    break;
+                }
+                tot[c] += ms;
+            }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    flush_lambda_kernel<<<h->nblk_flush, 256, 0, h->stream>>>(h->G, h->O);
-    clear_pending_kernel<<<(h->S + 255) / 256, 256, 0, h->stream>>>(h->G);
-    if ((rc = launch_check("flush_lambda_kernel")) != ADMM_OK) return rc;
+    // leave the solve where it was
+    if (rc == ADMM_OK) rc = replay_copy(h, snap, false);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == ADMM_OK) {
+        set_err("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = ADMM_ERR_CUDA;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    if (rc != ADMM_OK) return rc;
     int best = 0;
-    for (int c = 1; c < 5; ++c)
+    for (int c = 1; c < kCand; ++c)
         if (tot[c] < tot[best]) best = c;
     const int nbk = cand[best] < need ? (cand[best] > 0 ? cand[best] : 1) : need;
     h->nblk_branch = nbk;
@@ -1059,9 +1108,8 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, dou
             h->opts.use_graph = 0;
         }
     }
-    CK(cudaStreamSynchronize(h->stream));
     if (chosen) *chosen = nbk;
-    if (ms_best) *ms_best = tot[best] / iters;
+    if (ms_best) *ms_best = tot[best] / (2.0 * iters);
     return ADMM_OK;
 }
 

@@ -89,3 +89,26 @@ def test_warm_slot_restart_matches_solo_warm_start():
     s.solve(tol=0.0, max_iter=7, warm_start=True)
     for a, r in zip(mine, snapshot(s)):
         assert np.array_equal(a, r)
+
+
+def test_autotune_changes_no_result():
+    """The tuner replays iterations from a saved copy and puts the state back:
+    the tuned handle's solve is bitwise the untuned one's."""
+    grids = [synth.tiny_grid(14), synth.sized_grid(800, seed=6)]
+    tuned = admm.Solver(grids, **TINY)
+    tuned.solve(tol=0.0, max_iter=4)
+    before = tuned.get_state()
+    blocks, ms = tuned.autotune(2)
+    assert blocks >= 1 and ms > 0.0
+    assert tuned.get_state() == before
+    tuned.solve(tol=0.0, max_iter=3, warm_start=True)
+    ref2 = admm.Solver(grids, **TINY)
+    ref2.solve(tol=0.0, max_iter=4)
+    ref2.solve(tol=0.0, max_iter=3, warm_start=True)
+    for k in range(len(grids)):
+        tuned.select(k)
+        ref2.select(k)
+        for a, r in zip(snapshot(tuned), snapshot(ref2)):
+            assert np.array_equal(a, r), k
+    for s in (tuned, ref2):
+        s.close()
