@@ -17,12 +17,13 @@
 // from a queue as soon as its branch is finished; each trip of the main loop
 // performs exactly one TRON iteration in every lane that has one to do, so the
 // expensive code runs with nearly full warps.  One lane solves one branch
-// entirely in registers (the Hessian packed, 21 entries; the TRON free set
-// handled with masks so all loops have fixed trip counts); the branch data the
-// evaluations read (admittances and targets) sit in shared memory.  The
-// function, gradient and Hessian are evaluated together at every trial point
-// (one sincos), since nearly every trial step is accepted; after a rejected
-// step the gradient and Hessian are re-evaluated at the kept point.
+// (its Hessian packed, 21 entries, in shared memory, everything else in
+// registers; the TRON free set handled with masks so all loops have fixed trip
+// counts); the branch data the evaluations read (admittances and targets) sit
+// in shared memory too.  The function, gradient and Hessian are evaluated
+// together at every trial point (one sincos), since nearly every trial step is
+// accepted; after a rejected step the gradient and Hessian are re-evaluated at
+// the kept point.
 #include "admm_internal.cuh"
 
 namespace admm {
@@ -38,6 +39,15 @@ __host__ __device__ constexpr int P(int i, int j)
 {
     return i <= j ? (i * (11 - i)) / 2 + j : (j * (11 - j)) / 2 + i;
 }
+
+// A lane's packed symmetric Hessian lives in shared memory, the block's lanes
+// interleaved (stride kBranchBlock): held in registers it costs 42 of the 255
+// a lane has, and the subspace step then spills; from shared memory the
+// 70,000-bus launch ran 6 % faster.
+struct SMat {
+    double *p;
+    __device__ __forceinline__ double &operator[](int k) const { return p[k * kBranchBlock]; }
+};
 
 struct Cnt {
     int tron_calls, tron_iters, fgh, f, cauchy, cg, ps, al, maxhit;
@@ -135,7 +145,7 @@ __device__ __forceinline__ void flow(double a, double al, double be, double vi, 
 // Y and t live in shared memory with stride kBranchBlock.
 __device__ __forceinline__ void evaluate(const double *sY, const double *sT, double rpq, double rva,
                                          double lt0, double lt1, double rt, const double *x,
-                                         double &f, double *g, double *H, double *F)
+                                         double &f, double *g, SMat H, double *F)
 {
     const double vi = x[0], vj = x[1];
     double s, c;
@@ -226,7 +236,7 @@ __device__ __forceinline__ double dot6(const double *a, const double *b)
     return s;
 }
 
-__device__ __forceinline__ void hmul(const double *H, const double *v, double *o)
+__device__ __forceinline__ void hmul(SMat H, const double *v, double *o)
 {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -238,7 +248,7 @@ __device__ __forceinline__ void hmul(const double *H, const double *v, double *o
 }
 
 // q(s) = g's + s'Hs/2 using the symmetry of H
-__device__ __forceinline__ double qmodel(const double *g, const double *H, const double *s)
+__device__ __forceinline__ double qmodel(const double *g, SMat H, const double *s)
 {
     double q = 0.0;
 #pragma unroll
@@ -266,7 +276,7 @@ __device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const
     return m;
 }
 
-__device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, const double *s,
+__device__ __forceinline__ bool cauchy_ok(const double *g, SMat H, const double *s,
                                           double delta2)
 {
     return dle(dot6(s, s), delta2) && dle(qmodel(g, H, s), kMu0 * dot6(g, s));
@@ -288,7 +298,7 @@ __device__ __forceinline__ bool cauchy_ok(const double *g, const double *H, cons
 // a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
 // once; trials past a breakpoint evaluate the projection in full.
 __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x, const double *g,
-                                       const double *H, double delta, double &alpha, double *s,
+                                       SMat H, double delta, double &alpha, double *s,
                                        Cnt &c)
 {
     bool path[6];
@@ -355,7 +365,7 @@ __device__ __forceinline__ double boundary_tau(const double *a, const double *pv
 // fixed variables); the diagonal of L keeps the reciprocal pivots.  Lanes
 // with keep == true leave L unchanged.  kPlain: D = I and sigma = 0.
 template <bool kPlain>
-__device__ __forceinline__ bool chol_pass(const double *H, const bool *fr, const double *dinv,
+__device__ __forceinline__ bool chol_pass(SMat H, const bool *fr, const double *dinv,
                                           double sigma, bool keep, double *L)
 {
     bool ok = true;
@@ -383,7 +393,7 @@ __device__ __forceinline__ bool chol_pass(const double *H, const bool *fr, const
 // until the factorisation succeeds (at most kCholTries passes).  A positive
 // definite block is first factored unscaled: then D L L' D = L0 L0' exactly,
 // so the preconditioned CG iterates are the same.
-__device__ __forceinline__ void precond_factor(bool on, const double *H, const bool *fr, double *L,
+__device__ __forceinline__ void precond_factor(bool on, SMat H, const bool *fr, double *L,
                                                double *dinv)
 {
 #pragma unroll
@@ -442,9 +452,10 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
 __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
-                                         const double *H, double delta, const double *sc,
-                                         double *s, Cnt &c)
+                                         SMat H, double delta, const double *sc,
+                                         double *s, double &qs, bool &qs_ok, Cnt &c)
 {
+    qs_ok = false;
     bool fr[6];
     double xc[6];
     bool any = false;
@@ -533,6 +544,8 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         for (int i = 0; i < 6; ++i) pv[i] = go ? z[i] + be * pv[i] : pv[i];
     }
     const double qc = qmodel(g, H, sc);
+    qs = qc;                 // q(s) for the step returned: the Cauchy point's, or
+    qs_ok = cgon;            // the accepted search point's below
     double beta = 1.0;
     bool ps = cgon;
     for (int t = 0; t < kPsTrials; ++t) {
@@ -544,9 +557,11 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
             sb[i] = B.clamp(i, xc[i] + beta * w[i]) - x[i];
             dd[i] = sb[i] - sc[i];
         }
-        const bool okp = ps && dle(qmodel(g, H, sb), qc + kMu0 * dot6(gc, dd));
+        const double qb = qmodel(g, H, sb);
+        const bool okp = ps && dle(qb, qc + kMu0 * dot6(gc, dd));
 #pragma unroll
         for (int i = 0; i < 6; ++i) s[i] = okp ? sb[i] : s[i];
+        qs = okp ? qb : qs;
         ps = ps && !okp;
         beta *= 0.5;
     }
@@ -594,6 +609,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
 {
     __shared__ double sh[16 * kBranchBlock];   // per lane: Y[8], t[8], stride kBranchBlock
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
+    __shared__ double shH[21 * kBranchBlock];  // per lane: packed Hessian
+    const SMat H{shH + threadIdx.x};
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
@@ -612,13 +629,17 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     }
     __syncthreads();
     const bool ordered = cstart[kClasses] == (unsigned)nl;
+    // positions [0, nspread) of the queue are dealt across wspread warps
+    const unsigned lanes = gridDim.x * blockDim.x;
+    const unsigned wspread = (lanes < (unsigned)nl ? lanes : (unsigned)nl) >> 5;
+    const unsigned nspread = wspread << 5;
     const int32_t *lcur = G.cls_list + (size_t)cur * kClasses * nl;
     int32_t *lnxt = G.cls_list + (size_t)nxt * kClasses * nl;
 
     int b = -1, state = LS_IDLE, apass = 0, k = 0, trips = 0;
     bool exhausted = false;
     Bounds B{1.0, 1.0, 1.0, 1.0, 0.0, 0, 0, 0, 0, 0};
-    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xt[6], g[6], H[21], F[4] = {0.0, 0.0, 0.0, 0.0};
+    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xt[6], g[6], F[4] = {0.0, 0.0, 0.0, 0.0};
     double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0, prered = 0.0, snorm = 0.0;
     double lt0 = 0.0, lt1 = 0.0, rt = rt0, hprev = 0.0;
 
@@ -639,8 +660,15 @@ branch_tron_kernel(DevGrid G, DevOpts O)
         }
         if (__any_sync(kFull, go_t)) {
             double sc[6], s[6];
+            double qs = 0.0;
+            bool qs_ok = false;
             cauchy(go_t, B, x, g, H, delta, alpha, sc, c);
-            subspace(go_t, B, x, g, H, delta, sc, s, c);
+            subspace(go_t, B, x, g, H, delta, sc, s, qs, qs_ok, c);
+            // q(s) is known unless the subspace step stopped at the Cauchy point
+            if (__any_sync(kFull, go_t && !qs_ok)) {
+                const double q2 = qmodel(g, H, s);
+                qs = qs_ok ? qs : q2;
+            }
             if (go_t) {
                 double xn = 0.0, sn = 0.0;
 #pragma unroll
@@ -651,7 +679,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 if (dle(sn, O.tron_xtol * dmaxi(xn, 1.0))) {
                     state = LS_DONE;
                 } else {
-                    prered = -qmodel(g, H, s);
+                    prered = -qs;
                     c.f++;
                     if (!dpos(prered)) {
                         state = LS_DONE;          // no decrease predicted: stalled
@@ -714,11 +742,16 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             if (state == LS_IDLE && !exhausted) {
                 const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
                 if (idx < (unsigned)nl) {
-                    int bb = (int)idx;
+                    // the first fill hands each warp 32 consecutive positions:
+                    // deal the ranks across warps instead (rank = lane-in-fill
+                    // x warps + warp), so the hardest branches spread over all
+                    // warps rather than filling the first ones
+                    const unsigned r = idx < nspread ? (idx & 31u) * wspread + (idx >> 5) : idx;
+                    int bb = (int)r;
                     if (ordered) {
                         int cl = 0;
-                        for (int q = 1; q < kClasses; ++q) cl = idx >= cstart[q] ? q : cl;
-                        bb = lcur[(size_t)cl * nl + (idx - cstart[cl])];
+                        for (int q = 1; q < kClasses; ++q) cl = r >= cstart[q] ? q : cl;
+                        bb = lcur[(size_t)cl * nl + (r - cstart[cl])];
                     }
                     const SCtrl *sc = G.sc + G.br_scen[bb];
                     if (!sc->active || sc->done) {
