@@ -50,6 +50,30 @@ def algorithmic_flops(stats: dict) -> float:
             + FLOPS["al"] * stats["al_passes"])
 
 
+# DRAM bytes (read + write) of one branch_tron launch of the default workload
+# (70,000 buses, seed 1) from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum).  Reported only while the kernel source is the one
+# the counters were taken on; any change to it makes the figure stale (null).
+TRAFFIC_CAPTURE = {"nbus": 70000, "seed": 1,
+                   "source_sha256": "90dd2944fb28e8362778bbe020c48650c758abdd50169f56d86c6acdc17f09df",
+                   "bytes_per_launch": 22.228224e6 + 0.528128e6}
+
+
+def branch_tron_traffic(args):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2110_06879_gb300",
+                       "csrc", "branch_tron.cu")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    c = TRAFFIC_CAPTURE
+    if digest != c["source_sha256"] or args.nbus != c["nbus"] or args.seed != c["seed"]:
+        return None
+    return c["bytes_per_launch"]
+
+
 def fp64_peak_gflops():
     """FP64 peak of a GB300 from unit counts and clock: 152 SMs x 4 sub-
     partitions x 0.5 FP64 FMA per clock (one warp instruction per 64 cycles
@@ -332,6 +356,25 @@ def run_ours(args):
               "objective": sol["objective"], "max_viol": sol["max_viol"],
               "graph_launches": 1}
 
+    # the one-level variant (z = 0, Mhanna et al.) on the same grid, as a speed
+    # comparison: time to the same tolerance from a cold start
+    tt1 = None
+    if args.time_to_tol and args.one_level:
+        s1 = admm.Solver(grid, stream=stream, two_level=0, **opts)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s1.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        r = s1.residuals()
+        sol = s1.solution()
+        secs = ev0.elapsed_time(ev1) / 1e3
+        tt1 = {"tol": 1e-3, "seconds": secs, "iters": r["iters"], "iters_per_s": r["iters"] / secs,
+               "status": admm.lib().admm_status_string(r["status"]).decode(),
+               "primal": r["primal"], "dual": r["dual"], "objective": sol["objective"],
+               "max_viol": sol["max_viol"]}
+        s1.close()
+
     # warm-start tracking: 10k-bus grid, AR(1) load snapshots, renewable ramps,
     # 2% ramp limit, each snapshot warm-started (Section IV-C)
     track = None
@@ -361,7 +404,8 @@ def run_ours(args):
                 "data": "synthetic", "config": workload_config(grid, opts, args),
                 "roofline": {"kernel": "branch_tron", "bound": "alu", "achieved": achieved,
                              "peak": peak, "unit": "GFLOP/s (FP64)", "frac": achieved / peak,
-                             "traffic": None, "ms_per_launch": b_mean,
+                             "traffic": branch_tron_traffic(args), "traffic_unit": "bytes",
+                             "ms_per_launch": b_mean,
                              "flops_per_launch": flops_per_launch},
                 "bus_dual_ms": sum(bus_ms) / len(bus_ms),
                 "branch_solves_per_s": value * grid.nbranch,
@@ -369,6 +413,8 @@ def run_ours(args):
                 "tron_stats_per_step": {k: v / args.steps for k, v in stats_acc.items()}}
         if tt is not None:
             line["time_to_tol"] = tt
+        if tt1 is not None:
+            line["time_to_tol_one_level"] = tt1
         if track is not None:
             line["tracking"] = track
         if batched is not None:
@@ -398,6 +444,8 @@ def main():
     ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false")
     ap.add_argument("--tol-max-iter", type=int, default=5000)
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
+    ap.add_argument("--no-one-level", dest="one_level", action="store_false",
+                    help="skip the one-level (z = 0) time-to-tolerance comparison")
     ap.add_argument("--batched", type=int, default=0,
                     help="add the batched leg with this many scenarios (256 in the workload)")
     ap.add_argument("--batch-sample", type=int, default=8)

@@ -112,3 +112,19 @@ def test_autotune_changes_no_result():
             assert np.array_equal(a, r), k
     for s in (tuned, ref2):
         s.close()
+
+
+@pytest.mark.parametrize("blocks", [1, 3, 40])
+def test_branch_block_count_changes_no_result(blocks):
+    """The branch queue order (longest first, first fill dealt across warps)
+    and the number of resident blocks decide only which lane solves which
+    branch, never a value: iterates are bitwise the same."""
+    grid = synth.sized_grid(2000, seed=7)
+    ref = admm.Solver(grid, rho_pq=3e3, rho_va=3e4)
+    ref.solve(tol=0.0, max_iter=6)
+    s = admm.Solver(grid, rho_pq=3e3, rho_va=3e4, branch_blocks=blocks)
+    s.solve(tol=0.0, max_iter=6)
+    for a, r in zip(snapshot(s), snapshot(ref)):
+        assert np.array_equal(a, r)
+    s.close()
+    ref.close()
