@@ -629,10 +629,9 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     }
     __syncthreads();
     const bool ordered = cstart[kClasses] == (unsigned)nl;
-    // positions [0, nspread) of the queue are dealt across wspread warps
+    // the first `lanes` positions of the queue are dealt across all warps
     const unsigned lanes = gridDim.x * blockDim.x;
-    const unsigned wspread = (lanes < (unsigned)nl ? lanes : (unsigned)nl) >> 5;
-    const unsigned nspread = wspread << 5;
+    const unsigned nwarps = lanes >> 5;
     const int32_t *lcur = G.cls_list + (size_t)cur * kClasses * nl;
     int32_t *lnxt = G.cls_list + (size_t)nxt * kClasses * nl;
 
@@ -741,12 +740,16 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             int skip = -1;
             if (state == LS_IDLE && !exhausted) {
                 const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
-                if (idx < (unsigned)nl) {
-                    // the first fill hands each warp 32 consecutive positions:
-                    // deal the ranks across warps instead (rank = lane-in-fill
-                    // x warps + warp), so the hardest branches spread over all
-                    // warps rather than filling the first ones
-                    const unsigned r = idx < nspread ? (idx & 31u) * wspread + (idx >> 5) : idx;
+                // the first fill hands each warp 32 consecutive positions:
+                // deal the ranks across the warps instead (rank = lane-in-fill
+                // x warps + warp), so that the hardest branches spread over all
+                // warps rather than filling the first ones, and a grid with
+                // fewer branches than lanes occupies every warp.  Positions
+                // whose rank is past the end hold no branch; every position
+                // below `lanes` is still drawn, since each lane draws at least
+                // once and draws take consecutive positions.
+                const unsigned r = idx < lanes ? (idx & 31u) * nwarps + (idx >> 5) : idx;
+                if (r < (unsigned)nl) {
                     int bb = (int)r;
                     if (ordered) {
                         int cl = 0;
