@@ -207,7 +207,7 @@ def run_batched(args, admm, stream):
     grids = synth.batch_grids(args.batched, lo=500, hi=20000, seed=args.seed)
     kw = dict(rho_pq=3e3, rho_va=3e4)
     b = admm.Solver(grids, stream=stream, **kw)
-    blocks, _ = b.autotune(2)
+    blocks, body, _ = b.autotune(2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.solve(tol=1e-3, max_iter=3000)        # cold start of every scenario
@@ -228,7 +228,7 @@ def run_batched(args, admm, stream):
             "branches": int(sum(g.nbranch for g in grids)), "seconds": dt,
             "scenarios_per_s": len(grids) / dt, "converged": int((st == 0).sum()),
             "iters_p50": int(np.median(it)), "iters_max": int(it.max()),
-            "autotuned_branch_blocks": blocks,
+            "autotuned_branch_blocks": blocks, "autotuned_graph_body_iters": body,
             "plain_loop_sample": len(sample), "plain_loop_scenarios_per_s": len(sample) / tloop,
             "speedup_vs_plain_loop": (len(grids) / dt) / (len(sample) / tloop),
             "tol": 1e-3, "max_iter": 3000, "rho_pq": kw["rho_pq"], "rho_va": kw["rho_va"]}

@@ -97,7 +97,10 @@ typedef struct {
     int32_t al_max_iter;   /* 20 */
     int32_t tron_max_iter; /* 200 */
     int32_t use_graph;     /* 1: conditional-WHILE CUDA graph; 0: stream launches   */
-    int32_t branch_blocks; /* resident blocks of 128 branch lanes; 0: 2 per SM          */
+    int32_t branch_blocks; /* resident blocks of 128 branch lanes; 0: one per SM       */
+    int32_t graph_body_iters; /* iterations per body of the WHILE node, 1..16 (1); the
+                                 loop still stops after exactly the iteration that
+                                 converges or reaches max_iter                       */
 } admm_options;
 
 typedef struct {
@@ -279,16 +282,23 @@ int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
                              const double *d_lambda, double beta, int32_t two_level,
                              double *d_z, double *d_y, double *d_norms, void *cuda_stream);
 
-/* Autotuner: times the branch_tron launch for 5 resident-block counts (1/2,
- * 3/4, 1, 3/2 and 2 blocks of 128 lanes per SM) and keeps the fastest for
- * later solves (the iteration graph is rebuilt).  Every candidate replays the
- * same `iters` warm iterations of every scenario from a device copy of the
- * current state, twice (forward and reverse candidate order); afterwards the
- * state is put back, so the tuner changes no result and no iteration count.
- * It allocates one temporary device buffer the size of the iteration state
- * (ADMM_ERR_OOM if that fails).  *chosen (may be NULL) receives the block
- * count, *ms_best the fastest candidate's mean branch_tron time. */
-int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best);
+/* Autotuner over the launch shape, never over results.  (1) Resident
+ * branch_tron blocks: 5 counts (1/2, 3/4, 1, 3/2 and 2 blocks of 128 lanes
+ * per SM), each timed on the same `iters` warm iterations of every scenario
+ * replayed from a device copy of the current state, twice (forward and reverse
+ * order); the fastest mean branch_tron time wins.  (2) With the graph path,
+ * iterations per body of the WHILE node (1, 2, 4), each timed through the
+ * graph over 4 * iters replayed iterations.  The choice is kept for later
+ * solves (the graph is rebuilt) and the state is put back, so the tuner
+ * changes no result and no iteration count.  Lanes per branch are fixed at
+ * one: a branch's TRON iteration is a chain of dependent 6x6 operations and
+ * GB300's FP64 pipe costs the same per warp instruction at any lane count.
+ * Allocates one temporary device buffer the size of the iteration state
+ * (ADMM_ERR_OOM if that fails).  Outputs may be NULL: *blocks_out the block
+ * count, *body_out the iterations per graph body, *ms_best the fastest mean
+ * branch_tron time in ms. */
+int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
+                  double *ms_best);
 
 const char *admm_status_string(int status);
 /* Text of the last error recorded by any call in this process (thread-local). */

@@ -40,6 +40,7 @@ void set_err(const char *fmt, ...)
         }                                                                            \
     } while (0)
 
+constexpr int kMaxBodyIters = 16;
 constexpr uint64_t kStateMagic = 0x41444d4d53543032ull;   // "ADMMST02"
 
 }  // namespace
@@ -100,6 +101,7 @@ extern "C" void admm_default_options(admm_options *o)
     o->tron_max_iter = 200;
     o->use_graph = 1;
     o->branch_blocks = 0;
+    o->graph_body_iters = 1;
 }
 
 extern "C" const char *admm_last_error(void) { return g_err.c_str(); }
@@ -170,6 +172,10 @@ int validate(const admm_grid *g, const admm_options *o)
     if (o) {
         if (!(o->rho_pq > 0.0) || !(o->rho_va > 0.0)) { set_err("penalties must be positive"); return ADMM_ERR_INVALID_ARG; }
         if (o->branch_blocks < 0) { set_err("branch_blocks must be >= 0"); return ADMM_ERR_INVALID_ARG; }
+        if (o->graph_body_iters < 1 || o->graph_body_iters > kMaxBodyIters) {
+            set_err("graph_body_iters must be in 1..%d", kMaxBodyIters);
+            return ADMM_ERR_INVALID_ARG;
+        }
         if (o->max_outer < 1 || o->max_inner < 1 || o->tron_max_iter < 1 || o->al_max_iter < 1) {
             set_err("iteration caps must be >= 1");
             return ADMM_ERR_INVALID_ARG;
@@ -241,14 +247,11 @@ int build_graph(admm_handle *h)
     bp.gridDim = dim3(h->nblk_branch);
     bp.blockDim = dim3(kBranchBlock);
     bp.kernelParams = bargs;
-    cudaGraphNode_t bnode, unode, cnode, fnode, pnode;
-    CK(cudaGraphAddKernelNode(&bnode, body, nullptr, 0, &bp));
     cudaKernelNodeParams up{};
     up.func = (void *)bus_dual_kernel;
     up.gridDim = dim3(h->nblk_bus);
     up.blockDim = dim3(kBusBlock);
     up.kernelParams = bargs;
-    CK(cudaGraphAddKernelNode(&unode, body, &bnode, 1, &up));
     int32_t use_cond = 1;
     void *cargs[3] = {&h->G, &cond, &use_cond};
     cudaKernelNodeParams ccp{};
@@ -256,7 +259,14 @@ int build_graph(admm_handle *h)
     ccp.gridDim = dim3(1);
     ccp.blockDim = dim3(32);
     ccp.kernelParams = cargs;
-    CK(cudaGraphAddKernelNode(&cnode, body, &unode, 1, &ccp));
+    // graph_body_iters iterations per body: once a control kernel has set the
+    // device stop flag, the kernels after it in the body return at once
+    cudaGraphNode_t bnode, unode, cnode = nullptr, fnode, pnode;
+    for (int r = 0; r < h->opts.graph_body_iters; ++r) {
+        CK(cudaGraphAddKernelNode(&bnode, body, cnode ? &cnode : nullptr, cnode ? 1 : 0, &bp));
+        CK(cudaGraphAddKernelNode(&unode, body, &bnode, 1, &up));
+        CK(cudaGraphAddKernelNode(&cnode, body, &unode, 1, &ccp));
+    }
     cudaKernelNodeParams fp{};
     fp.func = (void *)flush_lambda_kernel;
     fp.gridDim = dim3(h->nblk_flush);
@@ -1032,7 +1042,8 @@ int replay_copy(admm_handle *h, char *snap, bool save)
 
 }  // namespace
 
-extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, double *ms_best)
+extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
+                             double *ms_best)
 {
     if (!h || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
     int dev = 0, sms = 152;
@@ -1083,6 +1094,49 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, dou
             }
         }
     }
+    int best = 0;
+    for (int c = 1; c < kCand; ++c)
+        if (tot[c] < tot[best]) best = c;
+    const int nbk = cand[best] < need ? (cand[best] > 0 ? cand[best] : 1) : need;
+    if (rc == ADMM_OK) {
+        h->nblk_branch = nbk;
+        h->G.nblk_branch = nbk;
+        h->opts.branch_blocks = nbk;
+    }
+    // graph shape: iterations per body of the WHILE node, timed through the
+    // graph itself over 4 * iters iterations replayed from the same state
+    constexpr int kBodyCand = 3;
+    const int bc[kBodyCand] = {1, 2, 4};
+    double bt[kBodyCand] = {0, 0, 0};
+    bool tuned_body = false;
+    if (rc == ADMM_OK && h->opts.use_graph) {
+        for (int pass = 0; pass < 2 && rc == ADMM_OK; ++pass) {
+            for (int k = 0; k < kBodyCand && rc == ADMM_OK; ++k) {
+                const int c = pass == 0 ? k : kBodyCand - 1 - k;
+                h->opts.graph_body_iters = bc[c];
+                destroy_graph(h);
+                if ((rc = build_graph(h)) != ADMM_OK) break;
+                if ((rc = replay_copy(h, snap, false)) != ADMM_OK) break;
+                if ((rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, 4 * iters, 1)) != ADMM_OK)
+                    break;
+                float ms = 0.f;
+                if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = ADMM_ERR_CUDA; break; }
+                if ((rc = run_async(h, 4 * iters)) != ADMM_OK) break;
+                if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    set_err("autotune timing failed");
+                    rc = ADMM_ERR_CUDA;
+                    break;
+                }
+                bt[c] += ms;
+            }
+        }
+        tuned_body = rc == ADMM_OK;
+    }
+    int bbest = 0;
+    for (int c = 1; c < kBodyCand; ++c)
+        if (bt[c] < bt[bbest]) bbest = c;
+    h->opts.graph_body_iters = tuned_body ? bc[bbest] : 1;
     // leave the solve where it was
     if (rc == ADMM_OK) rc = replay_copy(h, snap, false);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == ADMM_OK) {
@@ -1092,14 +1146,6 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, dou
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(snap);
-    if (rc != ADMM_OK) return rc;
-    int best = 0;
-    for (int c = 1; c < kCand; ++c)
-        if (tot[c] < tot[best]) best = c;
-    const int nbk = cand[best] < need ? (cand[best] > 0 ? cand[best] : 1) : need;
-    h->nblk_branch = nbk;
-    h->G.nblk_branch = nbk;
-    h->opts.branch_blocks = nbk;
     if (h->opts.use_graph) {
         destroy_graph(h);
         if (build_graph(h) != ADMM_OK) {
@@ -1108,7 +1154,9 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *chosen, dou
             h->opts.use_graph = 0;
         }
     }
-    if (chosen) *chosen = nbk;
+    if (rc != ADMM_OK) return rc;
+    if (blocks_out) *blocks_out = nbk;
+    if (body_out) *body_out = h->opts.graph_body_iters;
     if (ms_best) *ms_best = tot[best] / (2.0 * iters);
     return ADMM_OK;
 }

@@ -98,8 +98,8 @@ def test_autotune_changes_no_result():
     tuned = admm.Solver(grids, **TINY)
     tuned.solve(tol=0.0, max_iter=4)
     before = tuned.get_state()
-    blocks, ms = tuned.autotune(2)
-    assert blocks >= 1 and ms > 0.0
+    blocks, body, ms = tuned.autotune(2)
+    assert blocks >= 1 and body in (1, 2, 4) and ms > 0.0
     assert tuned.get_state() == before
     tuned.solve(tol=0.0, max_iter=3, warm_start=True)
     ref2 = admm.Solver(grids, **TINY)
@@ -128,3 +128,21 @@ def test_branch_block_count_changes_no_result(blocks):
         assert np.array_equal(a, r)
     s.close()
     ref.close()
+
+
+@pytest.mark.parametrize("body", [2, 3])
+def test_graph_body_iterations_change_no_result(body):
+    """Several iterations per WHILE body stop after exactly the same iteration
+    (by the iteration cap mid-body, and by convergence), bitwise."""
+    grid = synth.tiny_grid(15)
+    for tol, cap in ((0.0, 7), (1e-4, 400)):
+        ref = admm.Solver(grid, **TINY)
+        st_ref = ref.solve(tol=tol, max_iter=cap)
+        s = admm.Solver(grid, graph_body_iters=body, **TINY)
+        st = s.solve(tol=tol, max_iter=cap)
+        assert st == st_ref
+        for a, r in zip(snapshot(s), snapshot(ref)):
+            assert np.array_equal(a, r)
+        assert np.array_equal(s.history(), ref.history())
+        s.close()
+        ref.close()
