@@ -55,8 +55,8 @@ def algorithmic_flops(stats: dict) -> float:
 # dram__bytes_write.sum).  Reported only while the kernel source is the one
 # the counters were taken on; any change to it makes the figure stale (null).
 TRAFFIC_CAPTURE = {"nbus": 70000, "seed": 1,
-                   "source_sha256": "90dd2944fb28e8362778bbe020c48650c758abdd50169f56d86c6acdc17f09df",
-                   "bytes_per_launch": 22.228224e6 + 0.528128e6}
+                   "source_sha256": "afba8c4d82bfe21d8d713faad67964738357ece6d0360ce7bed0070a7ac9780e",
+                   "bytes_per_launch": 22.229248e6 + 0.570112e6}
 
 
 def branch_tron_traffic(args):
@@ -134,6 +134,22 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def whole_job_rate(t_local_s, steps, device=None):
+    """Replicas: every rank times its own `steps`; the whole job's rate is the
+    steps all ranks processed over the slowest rank's time (max over ranks,
+    the one collective of the bench, outside the timed region).  Returns
+    (rate, max time)."""
+    import torch
+    import torch.distributed as dist
+    ws, t = 1, float(t_local_s)
+    if dist.is_available() and dist.is_initialized():
+        ws = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return ws * steps / t, t
 
 
 def make_workload(nbus, seed):
@@ -308,12 +324,7 @@ def run_ours(args):
             iter_ms.append(p["iter_ms"])
         torch.cuda.synchronize()
     clocks = clk.summary()
-    t_total = sum(iter_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = ws * args.steps / t_total
+    value, t_total = whole_job_rate(sum(iter_ms) / 1e3, args.steps, device=dev)
 
     # dominant kernel roofline (FP64 ALU bound)
     b_mean = sum(branch_ms) / len(branch_ms)

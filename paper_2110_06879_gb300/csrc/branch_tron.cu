@@ -600,7 +600,9 @@ __device__ __forceinline__ void file_branches(Ctrl *ctrl, int32_t *lnxt, int nl,
     }
 }
 
-enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE = 4 };
+// LS_REEVAL_DONE: the solve stopped right after a rejected step; the flows the
+// AL update needs are re-evaluated at the kept point first
+enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE = 4, LS_REEVAL_DONE = 5 };
 
 }  // namespace
 
@@ -806,7 +808,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 xt[i] = x[i];
             }
             eval = true;
-        } else if (state == LS_REEVAL) {
+        } else if (state == LS_REEVAL || state == LS_REEVAL_DONE) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) xt[i] = x[i];
             eval = true;
@@ -829,6 +831,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             state = LS_ITER;
         } else if (state == LS_REEVAL) {
             state = LS_ITER;
+        } else if (state == LS_REEVAL_DONE) {
+            state = LS_DONE;
         } else if (state == LS_ITER && eval) {
             const double actred = f - fe;
             if (k == 0 && dlt(snorm, delta)) delta = snorm;
@@ -847,7 +851,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             double xn = 0.0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) xn = amax(xn, x[i]);
-            if (dle(delta, 1e-14 * dmaxi(xn, 1.0))) state = LS_DONE;
+            if (dle(delta, 1e-14 * dmaxi(xn, 1.0)))
+                state = state == LS_REEVAL ? LS_REEVAL_DONE : LS_DONE;
             ++k;
         }
     }
