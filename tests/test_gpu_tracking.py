@@ -52,7 +52,7 @@ def test_tracking_sequence_matches_oracle():
         assert np.all(pg <= pmaxs[t] + 1e-12)
 
 
-def test_tracking_driver_converges_warm():
+def test_tracking_loop_converges_warm():
     grid = synth.tiny_grid(9)
     steps = 5
     pds, qds = synth.ar1_loads(grid, steps, seed=9)
