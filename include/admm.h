@@ -257,7 +257,7 @@ int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out);
  * memory is fixed once at start-up, or a program whose device memory all
  * belongs to another allocator and which must not let a library allocate
  * behind its back.  This entry point runs the z update, the y update and the
- * residual reduction of one inner iteration (lines 5-6 of Algorithm 1) on
+ * residual reduction of one inner iteration (the z- and y-updates of Algorithm 1) on
  * buffers the caller owns, and allocates nothing: its only scratch (per-block
  * partial sums and a ticket counter) is a static device array of 128 KiB +
  * 32 B that every GPU loading the library keeps until the process exits.

@@ -723,7 +723,7 @@ void ora_set_ramp_limit(ora *p, double frac)
     }
 }
 
-/* Algorithm 1 line 3, generators: eq. qp-bound with the scaled cost */
+/* Algorithm 1, x-update of the generators: eq. qp-bound with the scaled cost */
 static void update_generators(ora *p)
 {
     double so = p->o.obj_scale;
@@ -736,7 +736,7 @@ static void update_generators(ora *p)
     }
 }
 
-/* Algorithm 1 line 3, branches: eq. branch by the AL loop around TRON,
+/* Algorithm 1, x-update of the branches: eq. branch by the AL loop around TRON,
  * warm-started from the branch's previous solution clipped to its bounds */
 static void update_branches(ora *p, int l0, int l1)
 {
@@ -765,7 +765,7 @@ static void update_branches(ora *p, int l0, int l1)
     }
 }
 
-/* Algorithm 1 line 4: eq. qp-bus per bus.  The bus variables are the pooled
+/* Algorithm 1, xbar-update: eq. qp-bus per bus.  The bus variables are the pooled
  * w_i and theta_i and one copy per incident generator (p, q) and branch end
  * (p, q of the flow leaving bus i).  Coupling c contributes
  * rho_c/2 (xbar - t_c)^2 with target t_c = u_c + z_c + y_c/rho_c, so
@@ -846,7 +846,7 @@ static void update_buses(ora *p)
     free(Qd); free(cv); free(A0); free(A1); free(cpl);
 }
 
-/* One inner iteration of Algorithm 1 (lines 3-6) with its residuals:
+/* One inner iteration of Algorithm 1 (x-, xbar-, z- and y-updates) with its residuals:
  * primal = ||u - xbar||, primal_z = ||u - xbar + z||,
  * dual = ||rho (xbar - xbar_prev)||, zn = ||z||, all Euclidean. */
 static void iterate(ora *p, int l0, int l1)
@@ -859,7 +859,7 @@ static void iterate(ora *p, int l0, int l1)
     double sp = 0.0, spz = 0.0, sd = 0.0, sz = 0.0, su = 0.0, sx = 0.0, sy = 0.0;
     for (int c = 0; c < m; ++c) {
         double r0 = p->u[c] - p->xbar[c];
-        /* Algorithm 1 line 5: eq. qp-bound with (l, u) = (-inf, inf):
+        /* Algorithm 1, z-update: eq. qp-bound with (l, u) = (-inf, inf):
          * minimise lam z + beta/2 z^2 + y (r0 + z) + rho/2 (r0 + z)^2 */
         if (p->o.two_level) {
             double Q = p->beta + p->rho[c];
@@ -868,7 +868,7 @@ static void iterate(ora *p, int l0, int l1)
         } else {
             p->z[c] = 0.0;
         }
-        /* Algorithm 1 line 6: y <- y + rho (A x + B xbar + z) */
+        /* Algorithm 1, y-update: y <- y + rho (A x + B xbar + z) */
         p->y[c] += p->rho[c] * (r0 + p->z[c]);
         double dx = p->rho[c] * (p->xbar[c] - xprev[c]);
         sp += r0 * r0;
@@ -901,7 +901,7 @@ static double eps_pri(const ora *p, double t)
 }
 static double eps_dual(const ora *p, double t) { return sqrt((double)p->m) * t + t * p->ny; }
 
-/* Algorithm 1 line 8 (outer level, readings of this implementation):
+/* Algorithm 1, outer update (readings of this implementation):
  * lam <- Proj_[-lambda_max, lambda_max](lam + beta z); beta <- beta_factor beta
  * (capped) when ||z|| did not fall below z_decay times its value at the
  * previous outer update; the inner tolerance halves each outer update. */

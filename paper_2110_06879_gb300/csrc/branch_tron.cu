@@ -1,4 +1,4 @@
-// branch_tron: the branch x-update of Algorithm 1 (line 3).  Every branch
+// branch_tron: the branch part of the x-update of Algorithm 1.  Every branch
 // solves eq. branch (Section II-C): minimise over
 // x = (v_i, v_j, theta_i(ij), theta_j(ij), s_ij, s_ji) within bounds
 //   sum_c rho_c/2 (u_c(x) - t_c)^2 + sum_e [lt_e h_e + rt/2 h_e^2],

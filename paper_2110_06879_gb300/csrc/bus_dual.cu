@@ -1,4 +1,4 @@
-// bus_dual: lines 3 (generators), 4 (buses), 5 (z) and 6 (y) of Algorithm 1
+// bus_dual: the generator x-update, the bus xbar-update, the z-update and the y-update of Algorithm 1
 // fused into one pass over the bus -> incident-component CSR map, plus the
 // residual reduction and the loop control of the two-level algorithm.
 //

@@ -279,7 +279,7 @@ def test_bus_update_dense_kkt(oracle_mod):
 
 
 def test_z_and_y_updates(oracle_mod):
-    """Line 5-6 of Algorithm 1: z is the stationary point of
+    """The z- and y-updates of Algorithm 1: z is the stationary point of
     lam z + beta/2 z^2 + y (r0 + z) + rho/2 (r0 + z)^2; y += rho (r0 + z)."""
     grid = synth.tiny_grid(2)
     kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5, tol_in0=1e-12)   # no outer step yet
@@ -301,7 +301,7 @@ def test_z_and_y_updates(oracle_mod):
 
 
 def test_outer_update_rule(oracle_mod):
-    """Algorithm 1 line 8 with max_inner = 1: one outer update per iteration.
+    """The outer update of Algorithm 1 with max_inner = 1: one per iteration.
     lam <- Proj(lam + beta z); beta grows by beta_factor only when ||z|| did
     not drop below z_decay of its value at the previous outer update."""
     grid = synth.tiny_grid(2)
