@@ -473,7 +473,7 @@ def main():
     ap.add_argument("--batch-sample", type=int, default=8)
     ap.add_argument("--served", action="store_true", help="add the continuous-batching leg")
     ap.add_argument("--pool", type=int, default=32)
-    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--mem-budget-gb", type=int, default=16)
     ap.add_argument("--track-steps", type=int, default=60)

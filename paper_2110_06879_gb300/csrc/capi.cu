@@ -3,6 +3,7 @@
 // the copy-out of results.  All numerical work runs in the kernels of
 // branch_tron.cu and bus_dual.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -13,6 +14,16 @@
 
 #include "../../include/admm.h"
 #include "admm_internal.cuh"
+
+namespace {
+// NVTX range around one C-ABI call, for Nsight timelines (no cost without a tool)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace admm;
 
@@ -363,6 +374,7 @@ int sync_sc(admm_handle *h)
 extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const admm_options *o,
                                  admm_handle **out)
 {
+    NvtxRange nvtx_("admm_create_batch");
     if (!out) { set_err("out is NULL"); return ADMM_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!grids || nscen < 1) { set_err("need at least one grid"); return ADMM_ERR_INVALID_ARG; }
@@ -640,6 +652,7 @@ extern "C" int admm_set_stream(admm_handle *h, void *s)
 
 extern "C" int admm_set_loads(admm_handle *h, const double *pd, const double *qd)
 {
+    NvtxRange nvtx_("admm_set_loads");
     if (!h || !pd || !qd) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
     const int i0 = h->bus_off[h->sel], n = h->bus_off[h->sel + 1] - i0;
     if (!finite_all(pd, n) || !finite_all(qd, n)) { set_err("loads not finite"); return ADMM_ERR_INVALID_ARG; }
@@ -688,6 +701,7 @@ extern "C" int admm_set_ramp_limit(admm_handle *h, double frac)
 extern "C" int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, double tol,
                                 int32_t max_iter, int32_t warm_start)
 {
+    NvtxRange nvtx_("admm_solve_async");
     if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
     if (!(rho_pq > 0.0) || !(rho_va > 0.0) || !(tol >= 0.0) || max_iter < 0) {
         set_err("need rho > 0, tol >= 0, max_iter >= 0");
@@ -704,6 +718,7 @@ extern "C" int admm_solve_async(admm_handle *h, double rho_pq, double rho_va, do
 extern "C" int admm_solve(admm_handle *h, double rho_pq, double rho_va, double tol, int32_t max_iter,
                           int32_t warm_start)
 {
+    NvtxRange nvtx_("admm_solve");
     int rc = admm_solve_async(h, rho_pq, rho_va, tol, max_iter, warm_start);
     if (rc != ADMM_OK) return rc;
     if ((rc = sync_sc(h)) != ADMM_OK) return rc;
@@ -720,6 +735,7 @@ extern "C" int admm_solve(admm_handle *h, double rho_pq, double rho_va, double t
 extern "C" int admm_slot_begin(admm_handle *h, int32_t s, double rho_pq, double rho_va, double tol,
                                int32_t max_iter, int32_t warm_start)
 {
+    NvtxRange nvtx_("admm_slot_begin");
     if (!h || s < 0 || s >= h->S) { set_err("scenario out of range"); return ADMM_ERR_INVALID_ARG; }
     if (!(rho_pq > 0.0) || !(rho_va > 0.0) || !(tol >= 0.0) || max_iter < 0) {
         set_err("need rho > 0, tol >= 0, max_iter >= 0");
@@ -730,6 +746,7 @@ extern "C" int admm_slot_begin(admm_handle *h, int32_t s, double rho_pq, double 
 
 extern "C" int admm_run(admm_handle *h, int32_t max_iters)
 {
+    NvtxRange nvtx_("admm_run");
     if (!h || max_iters < 0) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
     if (max_iters == 0) return ADMM_OK;
     return run_async(h, max_iters);
@@ -773,6 +790,7 @@ extern "C" int admm_get_residuals(admm_handle *h, admm_residuals *out)
 extern "C" int admm_get_solution(admm_handle *h, double *pg, double *qg, double *vm, double *va,
                                  double *pf, double *qf, double *pt, double *qt)
 {
+    NvtxRange nvtx_("admm_get_solution");
     if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
     const Range R = range_of(h, h->sel);
     const int nb = R.i1 - R.i0, nl = R.b1 - R.b0, ng = R.g1 - R.g0;
@@ -947,6 +965,7 @@ constexpr int kScalarsPerScenario = 4;   // beta, total iterations, beta_used, p
 
 extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
 {
+    NvtxRange nvtx_("admm_get_state");
     if (!h || !len) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
     auto parts = state_parts(h);
     size_t n = 0;
@@ -980,6 +999,7 @@ extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
 
 extern "C" int admm_set_state(admm_handle *h, const void *buf, size_t len)
 {
+    NvtxRange nvtx_("admm_set_state");
     if (!h || !buf) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
     auto parts = state_parts(h);
     size_t n = 0;
@@ -1045,6 +1065,7 @@ int replay_copy(admm_handle *h, char *snap, bool save)
 extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
                              double *ms_best)
 {
+    NvtxRange nvtx_("admm_autotune");
     if (!h || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1163,6 +1184,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
 
 extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out)
 {
+    NvtxRange nvtx_("admm_profile_iterations");
     if (!h || !ms_out || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
     int rc = slot_begin(h, 0, h->S, h->opts.rho_pq, h->opts.rho_va, 0.0, iters, 1);
     if (rc != ADMM_OK) return rc;
