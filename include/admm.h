@@ -8,7 +8,8 @@
  * admm_create_batch) -- resident on the current CUDA device.  Every iteration
  * of Algorithm 1 runs on the device, for all scenarios at once:
  *   branch_tron  -- eq. branch per branch (TRON inside an augmented Lagrangian on
- *                   the line limits, Section II-C / III-B), one thread per branch;
+ *                   the line limits, Section II-C / III-B); a persistent launch in
+ *                   which each lane solves one branch at a time from a work queue;
  *   bus_dual     -- eq. qp-bound for generators, eq. qp-bus per bus over a CSR
  *                   incidence map (no atomics), the z update (eq. qp-bound with
  *                   infinite bounds), the y update (Section III-B) and the
