@@ -152,6 +152,28 @@ def test_tron_kkt(oracle_mod):
         assert pg <= 1e-10 * max(1.0, np.abs(g0).max()), (it, pg, st)
 
 
+def test_tron_carried_alpha_changes_path_not_point(oracle_mod):
+    """The Cauchy search of a TRON call starts from the alpha the branch's
+    previous call ended with.  That alpha only steers the search: from starts
+    of 1e-8, 1 and 1e4 the solves end at points satisfying the same KKT test,
+    equal to within a tolerance set by it, and hand back a positive alpha."""
+    rng = np.random.default_rng(21)
+    for it in range(60):
+        bp, x0, _ = _random_prob(oracle_mod, rng, rate=0.3 if it % 3 == 0 else None)
+        _, g0, _ = oracle_mod.branch_fgh(bp, x0)
+        lo, hi = np.array(bp.lo[:]), np.array(bp.hi[:])
+        xs = []
+        for a0 in (1e-8, 1.0, 1e4):
+            bp.alpha = a0
+            x, status, _ = oracle_mod.tron(bp, x0)
+            assert status == 0 and bp.alpha > 0.0
+            _, g, _ = oracle_mod.branch_fgh(bp, x)
+            assert np.abs(_proj_grad(x, g, lo, hi)).max() <= 1e-10 * max(1.0, np.abs(g0).max())
+            xs.append(x)
+        for x in xs[1:]:
+            assert np.abs(x - xs[0]).max() <= 1e-7 * max(1.0, np.abs(xs[0]).max()), it
+
+
 def test_tron_brute_force_small(oracle_mod):
     """TRON's local solution is the best point of a 4-D grid search (slacks
     eliminated in closed form) refined by a local solve, or at least as good."""
