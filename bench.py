@@ -22,6 +22,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# kernels of this library launched per timed step (admm_profile_iterations of
+# one iteration): slot_begin, run_begin, branch_tron, bus_dual, control,
+# flush_lambda, clear_pending
+LAUNCHES_PER_STEP = 7
 METRIC = "ADMM iterations/s, 70k-bus synthetic grid (plus time to 1e-3 and p50/p99 tracking latency)"
 C_RESIDUALS_BYTES = 72   # sizeof(admm_residuals): 4 int32 + 7 double
 UNIT = "iter/s"
@@ -431,7 +435,7 @@ def run_ours(args):
                              "flops_per_launch": flops_per_launch},
                 "bus_dual_ms": sum(bus_ms) / len(bus_ms),
                 "branch_solves_per_s": value * grid.nbranch,
-                "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * args.steps * ws,
+                "e2e": e2e, "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,
                 "tron_stats_per_step": {k: v / args.steps for k, v in stats_acc.items()}}
         if tt is not None:
             line["time_to_tol"] = tt
