@@ -108,10 +108,14 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}",
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        # let the sampler produce its first line before the timed region starts
+        t0 = time.perf_counter()
+        while self.p and time.perf_counter() - t0 < 2.0 and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
