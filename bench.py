@@ -290,6 +290,8 @@ def run_served(args, admm, stream):
                                          deadline=2 * args.serve_seconds)
     return {"pool": len(grids), "resident": len(srv.grid_ids), "resident_bytes": srv.bytes,
             "pool_buses": int(sum(sizes)), "rate_per_s": args.rate,
+            "autotuned_branch_blocks": srv.tuned[0] if srv.tuned else None,
+            "autotuned_graph_body_iters": srv.tuned[1] if srv.tuned else None,
             "arrival_seconds": args.serve_seconds, "pool_cold_solve_s": warm,
             "served": serve.summarize(recs, wall), "rejected": len(rejected),
             "serial": serve.summarize(recs2, wall2),

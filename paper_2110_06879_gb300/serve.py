@@ -59,11 +59,15 @@ class Server:
         self.tol, self.max_iter, self.tick = tol, max_iter, tick_iters
         self.rho = (rho_pq, rho_va)
         self.solver = admm.Solver(self.grids, stream=stream, rho_pq=rho_pq, rho_va=rho_va, **opts)
+        self.tuned = None
 
-    def warm_up(self, max_iter=5000):
-        """Cold-solve every resident grid once, all together; returns seconds."""
+    def warm_up(self, max_iter=5000, tune=True):
+        """Cold-solve every resident grid once, all together, then (tune) pick
+        the launch shape for the pool on replayed iterations (the tuner puts
+        the state back, so no result changes); returns seconds."""
         t0 = time.perf_counter()
         self.solver.solve(tol=self.tol, max_iter=max_iter)
+        self.tuned = self.solver.autotune(2) if tune else None
         return time.perf_counter() - t0
 
     def run(self, requests, deadline: float = float("inf")):
