@@ -131,6 +131,43 @@ def test_branch_gradient_hessian_finite_differences(oracle_mod):
         assert np.abs(H - H.T).max() <= 1e-12 * scale_H
 
 
+def _F_analytic(bp, x):
+    """eq. branch with the flows of eqs. (pij)-(qji) written out in real
+    trigonometric form, which is analytic in x and so takes complex steps."""
+    gii, bii, gij, bij, gji, bji, gjj, bjj = bp.Y[:]
+    vi, vj, th = x[0], x[1], x[2] - x[3]
+    c, sn = np.cos(th), np.sin(th)
+    u = np.array([gii * vi * vi + vi * vj * (gij * c + bij * sn),
+                  -bii * vi * vi + vi * vj * (gij * sn - bij * c),
+                  gjj * vj * vj + vi * vj * (gji * c - bji * sn),
+                  -bjj * vj * vj + vi * vj * (-gji * sn - bji * c),
+                  vi * vi, x[2], vj * vj, x[3]])
+    rr = u - np.array(bp.xbar[:]) + np.array(bp.z[:])
+    F = np.sum(np.array(bp.y[:]) * rr + 0.5 * np.array(bp.rho[:]) * rr * rr)
+    for e in range(2):
+        h = u[2 * e] ** 2 + u[2 * e + 1] ** 2 + x[4 + e]
+        F += bp.lt[e] * h + 0.5 * bp.rt * h * h
+    return F
+
+
+def test_branch_gradient_complex_step(oracle_mod):
+    """The oracle's analytic gradient against complex-step derivatives of an
+    independent restatement of eq. branch (no subtractive cancellation, so
+    exact to rounding), after checking the restatement against the oracle's
+    function value."""
+    rng = np.random.default_rng(17)
+    hstep = 1e-20
+    for _ in range(40):
+        bp, x0, _ = _random_prob(oracle_mod, rng)
+        x = x0 + rng.normal(0, 0.03, 6) * np.array([1, 1, 1, 1, 0, 0])
+        x[4:] = x0[4:] * rng.uniform(0.3, 0.9)
+        f, g, _ = oracle_mod.branch_fgh(bp, x)
+        assert _F_analytic(bp, x) == pytest.approx(f, rel=1e-12, abs=1e-10)
+        gcs = np.array([_F_analytic(bp, x + 1j * hstep * np.eye(6)[k]).imag / hstep
+                        for k in range(6)])
+        assert np.abs(gcs - g).max() <= 1e-13 * max(1.0, np.abs(g).max())
+
+
 def _proj_grad(x, g, lo, hi):
     return np.clip(x - g, lo, hi) - x
 
