@@ -298,7 +298,7 @@ __device__ __forceinline__ bool cauchy_ok(const double *g, SMat H, const double 
 // a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
 // once; trials past a breakpoint evaluate the projection in full.
 __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x, const double *g,
-                                       SMat H, double delta, double &alpha, double *s,
+                                       SMat H, double d2, double &alpha, double *s,
                                        Cnt &c)
 {
     bool path[6];
@@ -313,7 +313,6 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
     double hg[6];
     hmul(H, gp, hg);
     const double G2 = dot6(gp, gp), GHG = dot6(gp, hg);
-    const double d2 = delta * delta;
     // sufficient decrease and radius test at alpha = a (uniform across the warp)
     auto ok_at = [&](double a, bool need) -> bool {
         bool unc = true;
@@ -352,10 +351,10 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
     if (on) alpha = a;
 }
 
-__device__ __forceinline__ double boundary_tau(const double *a, const double *pv, double delta)
+__device__ __forceinline__ double boundary_tau(const double *a, const double *pv, double d2)
 {
     const double pp = dot6(pv, pv), ap = dot6(a, pv), aa = dot6(a, a);
-    const double rad = dmaxi(delta * delta - aa, 0.0);
+    const double rad = dmaxi(d2 - aa, 0.0);
     const double disc = sqrt(ap * ap + pp * rad);
     if (!dpos(pp)) return 0.0;
     return dpos(ap) ? rad / (ap + disc) : (disc - ap) / pp;
@@ -452,7 +451,7 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
 __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
-                                         SMat H, double delta, const double *sc,
+                                         SMat H, double d2, const double *sc,
                                          double *s, double &qs, bool &qs_ok, Cnt &c)
 {
     qs_ok = false;
@@ -492,7 +491,6 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         rz += r[i] * pv[i];
     }
     const double tol2 = kCgRtol * kCgRtol * rn0;
-    const double d2 = delta * delta;
     bool go = cgon;
     for (int it = 0; it < kCgMaxit; ++it) {
         if (!__any_sync(kFull, go)) break;
@@ -517,7 +515,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         // negative curvature or the trust-region boundary: stop on the boundary
         const bool bnd = go && (!dpos(kappa) || dle(d2, nx2));
         if (__any_sync(kFull, bnd)) {
-            const double tau = boundary_tau(cur, pv, delta);
+            const double tau = boundary_tau(cur, pv, d2);
 #pragma unroll
             for (int i = 0; i < 6; ++i) w[i] = bnd ? w[i] + tau * pv[i] : w[i];
         }
@@ -641,7 +639,9 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     bool exhausted = false;
     Bounds B{1.0, 1.0, 1.0, 1.0, 0.0, 0, 0, 0, 0, 0};
     double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xt[6], g[6], F[4] = {0.0, 0.0, 0.0, 0.0};
-    double f = 0.0, delta = 0.0, alpha = 1.0, gtol = 0.0, prered = 0.0, snorm = 0.0;
+    // the trust radius is kept squared (dsq): its tests and updates need only
+    // squares, which saves a square root per step
+    double f = 0.0, dsq = 0.0, alpha = 1.0, gtol = 0.0, prered = 0.0, snorm2 = 0.0;
     double lt0 = 0.0, lt1 = 0.0, rt = rt0, hprev = 0.0;
 
     while (true) {
@@ -663,8 +663,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             double sc[6], s[6];
             double qs = 0.0;
             bool qs_ok = false;
-            cauchy(go_t, B, x, g, H, delta, alpha, sc, c);
-            subspace(go_t, B, x, g, H, delta, sc, s, qs, qs_ok, c);
+            cauchy(go_t, B, x, g, H, dsq, alpha, sc, c);
+            subspace(go_t, B, x, g, H, dsq, sc, s, qs, qs_ok, c);
             // q(s) is known unless the subspace step stopped at the Cauchy point
             if (__any_sync(kFull, go_t && !qs_ok)) {
                 const double q2 = qmodel(g, H, s);
@@ -687,7 +687,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                     } else {
 #pragma unroll
                         for (int i = 0; i < 6; ++i) xt[i] = B.clamp(i, x[i] + s[i]);
-                        snorm = sqrt(dot6(s, s));
+                        snorm2 = dot6(s, s);
                         eval = true;
                     }
                 }
@@ -825,7 +825,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             gtol = O.tron_gtol * dmaxi(pgnorm(B, x, g), 1.0);
             double sp[6];
             pstep(B, x, g, 1.0, sp);
-            delta = sqrt(dot6(sp, sp));
+            dsq = dot6(sp, sp);
             alpha = dpos(alpha) ? alpha : 1.0;   // carried from the previous call
             k = 0;
             state = LS_ITER;
@@ -835,12 +835,17 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             state = LS_DONE;
         } else if (state == LS_ITER && eval) {
             const double actred = f - fe;
-            if (k == 0 && dlt(snorm, delta)) delta = snorm;
+            if (k == 0 && dlt(snorm2, dsq)) dsq = snorm2;
             const double fa = dmaxi(dabsi(f), 1.0);
-            const double ratio = dle(prered, O.tron_ftol * fa) ? 1.0 : actred / prered;
-            if (dlt(ratio, kEta1)) delta = kSigma1 * dmini(snorm, delta);
-            else if (dlt(kEta2, ratio)) delta = dmaxi(delta, kSigma3 * snorm);
-            if (dlt(kEta0, ratio)) {
+            // ratio = actred / prered (1 when the model is trusted) against
+            // eta0, eta1, eta2, compared as actred against eta prered (prered > 0)
+            const bool trusted = dle(prered, O.tron_ftol * fa);
+            const bool below1 = !trusted && dlt(actred, kEta1 * prered);
+            const bool above2 = trusted || dlt(kEta2 * prered, actred);
+            const bool above0 = trusted || dlt(kEta0 * prered, actred);
+            if (below1) dsq = (kSigma1 * kSigma1) * dmini(snorm2, dsq);
+            else if (above2) dsq = dmaxi(dsq, (kSigma3 * kSigma3) * snorm2);
+            if (above0) {
 #pragma unroll
                 for (int i = 0; i < 6; ++i) x[i] = xt[i];
                 f = fe;
@@ -851,7 +856,8 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             double xn = 0.0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) xn = amax(xn, x[i]);
-            if (dle(delta, 1e-14 * dmaxi(xn, 1.0)))
+            const double xm = dmaxi(xn, 1.0);
+            if (dle(dsq, 1e-28 * xm * xm))
                 state = state == LS_REEVAL ? LS_REEVAL_DONE : LS_DONE;
             ++k;
         }
