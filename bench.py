@@ -232,40 +232,81 @@ def workload_config(grid, opts, args):
             "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
 
 
-def run_batched(args, admm, stream):
+def shard_scenarios(sizes, ws, rank):
+    """Indices of the scenarios rank `rank` of `ws` solves: longest first onto
+    the least-loaded rank (load = buses), ties to the lower rank; disjoint,
+    covering, identical on every rank."""
+    load = [0] * ws
+    mine = []
+    for k in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(ws), key=lambda q: (load[q], q))
+        load[r] += sizes[k]
+        if r == rank:
+            mine.append(k)
+    return sorted(mine)
+
+
+def reduce_over_ranks(seconds, counts, device=None):
+    """Max of `seconds` and sums of `counts` (a dict of numbers) over ranks;
+    identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return seconds, dict(counts)
+    keys = sorted(counts)
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([float(counts[k]) for k in keys], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), {k: float(v) for k, v in zip(keys, c.tolist())}
+
+
+def run_batched(args, admm, stream, device=None):
     """Scenarios of uneven size in one batched handle (one persistent launch
     per iteration over the flattened component index, per-scenario stopping),
-    autotuned; against a loop of plain one-grid solves on a sample."""
+    autotuned; against a loop of plain one-grid solves on a sample.  With
+    several ranks the scenarios are sharded (longest first, balanced by bus
+    count) with no collective on the data path; the job's rate is all
+    scenarios over the slowest rank's time."""
     import numpy as np
     import torch
     from paper_2110_06879_gb300 import synth
-    grids = synth.batch_grids(args.batched, lo=500, hi=20000, seed=args.seed)
+    ws, rank, _ = dist_env()
+    grids_all = synth.batch_grids(args.batched, lo=500, hi=20000, seed=args.seed)
+    mine = shard_scenarios([g.nbus for g in grids_all], ws, rank)
+    grids = [grids_all[k] for k in mine]
     kw = dict(rho_pq=3e3, rho_va=3e4)
     b = admm.Solver(grids, stream=stream, **kw)
     blocks, body, _ = b.autotune(2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.solve(tol=1e-3, max_iter=3000)        # cold start of every scenario
-    dt = time.perf_counter() - t0
+    dt_local = time.perf_counter() - t0
     st, it = b.slot_status()
     b.close()
+    dt, tot = reduce_over_ranks(dt_local, {"scenarios": len(grids), "converged": int((st == 0).sum())},
+                                device=device)
     rng = np.random.default_rng(args.seed)
-    sample = rng.choice(len(grids), min(args.batch_sample, len(grids)), replace=False)
+    sample = rng.choice(len(grids_all), min(args.batch_sample, len(grids_all)), replace=False)
     tloop = 0.0
-    for k in sample:
-        s = admm.Solver(grids[int(k)], stream=stream, **kw)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        s.solve(tol=1e-3, max_iter=3000)
-        tloop += time.perf_counter() - t1
-        s.close()
-    return {"scenarios": len(grids), "buses": int(sum(g.nbus for g in grids)),
-            "branches": int(sum(g.nbranch for g in grids)), "seconds": dt,
-            "scenarios_per_s": len(grids) / dt, "converged": int((st == 0).sum()),
-            "iters_p50": int(np.median(it)), "iters_max": int(it.max()),
+    if rank == 0:
+        for k in sample:
+            s = admm.Solver(grids_all[int(k)], stream=stream, **kw)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s.solve(tol=1e-3, max_iter=3000)
+            tloop += time.perf_counter() - t1
+            s.close()
+    n_all = int(tot["scenarios"])
+    return {"scenarios": n_all, "buses": int(sum(g.nbus for g in grids_all)),
+            "branches": int(sum(g.nbranch for g in grids_all)), "seconds": dt,
+            "scenarios_per_s": n_all / dt, "converged": int(tot["converged"]),
+            "ranks": ws, "sharding": "longest first by buses, no collective on the data path",
+            "iters_p50": int(np.median(it)), "iters_max": int(it.max()),   # rank 0's scenarios
             "autotuned_branch_blocks": blocks, "autotuned_graph_body_iters": body,
-            "plain_loop_sample": len(sample), "plain_loop_scenarios_per_s": len(sample) / tloop,
-            "speedup_vs_plain_loop": (len(grids) / dt) / (len(sample) / tloop),
+            "plain_loop_sample": len(sample),
+            "plain_loop_scenarios_per_s": len(sample) / tloop if tloop > 0 else None,
+            "speedup_vs_plain_loop": (n_all / dt) / (len(sample) / tloop) if tloop > 0 else None,
             "tol": 1e-3, "max_iter": 3000, "rho_pq": kw["rho_pq"], "rho_va": kw["rho_va"]}
 
 
@@ -426,7 +467,7 @@ def run_ours(args):
                       "rho_pq": topts["rho_pq"], "rho_va": topts["rho_va"], "tol": 1e-3})
         ts.close()
 
-    batched = run_batched(args, admm, stream) if args.batched > 0 else None
+    batched = run_batched(args, admm, stream, device=dev) if args.batched > 0 else None
     served = run_served(args, admm, stream) if args.served else None
 
     if rank == 0:

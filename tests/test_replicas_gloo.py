@@ -15,6 +15,18 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _rank_reduce(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t, c = bench.reduce_over_ranks([3.0, 5.0][rank], {"scenarios": 10 + rank, "converged": rank})
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"reduce{rank}.txt"), "w") as f:
+        f.write(f"{t!r} {c['scenarios']!r} {c['converged']!r}\n")
+
+
 def _rank_main(rank, world, port, times, out_dir):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
@@ -51,3 +63,29 @@ def test_whole_job_rate_single_process():
     import bench
     rate, tmax = bench.whole_job_rate(0.25, steps=10)
     assert tmax == 0.25 and rate == pytest.approx(40.0)
+
+
+def test_shard_scenarios_partition_is_balanced_and_covering():
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    rng = np.random.default_rng(3)
+    sizes = list(np.exp(rng.uniform(np.log(500), np.log(20000), 256)).astype(int))
+    for ws in (1, 2, 3, 8):
+        parts = [bench.shard_scenarios(sizes, ws, r) for r in range(ws)]
+        flat = sorted(k for p in parts for k in p)
+        assert flat == list(range(len(sizes)))                 # disjoint and covering
+        loads = [sum(sizes[k] for k in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)           # longest-first balance
+        assert parts == [bench.shard_scenarios(sizes, ws, r) for r in range(ws)]
+
+
+def test_reduce_over_ranks_two_gloo_ranks(tmp_path):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_reduce, args=(2, port, str(tmp_path)), nprocs=2,
+                       start_method="spawn", join=True)
+    for rank in range(2):
+        t, n, conv = map(float, (tmp_path / f"reduce{rank}.txt").read_text().split())
+        assert (t, n, conv) == (5.0, 21.0, 1.0)
