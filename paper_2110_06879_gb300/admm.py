@@ -209,7 +209,15 @@ class Solver:
         _check(lib().admm_set_loads(self.h, _ptr(pd), _ptr(qd)), "admm_set_loads")
 
     def set_loads_device(self, d_pd, d_qd):
-        """Device pointers (ints) or torch float64 CUDA tensors."""
+        """Device pointers (ints) or contiguous float64 CUDA tensors of nbus
+        entries (those are checked here; raw pointers are the caller's)."""
+        for t in (d_pd, d_qd):
+            if hasattr(t, "data_ptr"):
+                ok = (str(t.dtype) == "torch.float64" and t.is_cuda and t.is_contiguous()
+                      and t.numel() == self.nb)
+                if not ok:
+                    raise AdmmError("set_loads_device: need contiguous float64 CUDA tensors "
+                                    f"of {self.nb} entries")
         p = getattr(d_pd, "data_ptr", lambda: d_pd)()
         q = getattr(d_qd, "data_ptr", lambda: d_qd)()
         _check(lib().admm_set_loads_device(self.h, C.c_void_p(p), C.c_void_p(q)),
