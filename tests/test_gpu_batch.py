@@ -146,3 +146,26 @@ def test_graph_body_iterations_change_no_result(body):
         assert np.array_equal(s.history(), ref.history())
         s.close()
         ref.close()
+
+
+def test_api_error_paths():
+    """Calls with arguments the handle cannot serve fail with an error, leave
+    the handle usable, and change no state."""
+    grids = [synth.tiny_grid(16), synth.tiny_grid(17)]
+    b = admm.Solver(grids, **TINY)
+    b.solve(tol=0.0, max_iter=3)
+    before = b.get_state()
+    with pytest.raises(admm.AdmmError):
+        b.select(2)                                   # no such scenario
+    with pytest.raises(admm.AdmmError):
+        b.set_state(before[:-8])                      # truncated blob
+    other = admm.Solver(synth.tiny_grid(18), **TINY)
+    with pytest.raises(admm.AdmmError):
+        other.set_state(before)                       # blob of another handle
+    with pytest.raises(admm.AdmmError):
+        b.slot_begin(5, tol=0.0, max_iter=3)          # no such slot
+    assert b.get_state() == before
+    b.select(1)
+    assert b.solve(tol=0.0, max_iter=2, warm_start=True) == admm.ADMM_NOT_CONVERGED
+    other.close()
+    b.close()
