@@ -310,32 +310,60 @@ def run_batched(args, admm, stream, device=None):
             "tol": 1e-3, "max_iter": 3000, "rho_pq": kw["rho_pq"], "rho_va": kw["rho_va"]}
 
 
+def gather_objects(obj):
+    """Every rank's `obj`, in rank order (just [obj] without a process group)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return [obj]
+    out = [None] * dist.get_world_size()
+    dist.all_gather_object(out, obj)
+    return out
+
+
 def run_served(args, admm, stream):
     """Continuous batching over a resident pool (log-uniform 1k-70k buses, one
     grid pinned at 70k) under Poisson load-snapshot requests, against the same
-    stream served by serial plain solves."""
+    stream served by serial plain solves.  With several ranks the pool is
+    sharded like the batched scenarios and each rank serves the requests for
+    its own grids; the records are gathered once at the end."""
+    import dataclasses
     import numpy as np
     from paper_2110_06879_gb300 import serve, synth
+    ws, rank, _ = dist_env()
     rng = np.random.Generator(np.random.PCG64(args.seed + 5))
     sizes = list(np.exp(rng.uniform(np.log(1000), np.log(70000), args.pool - 1)).astype(int))
     sizes.append(70000)
     grids = [synth.sized_grid(int(n), seed=500 + k) for k, n in enumerate(sizes)]
-    srv = serve.Server(grids, mem_budget=args.mem_budget_gb << 30, tick_iters=8, max_iter=500,
+    mine = shard_scenarios(sizes, ws, rank)
+    local = {k: i for i, k in enumerate(mine)}
+    my_grids = [grids[k] for k in mine]
+    srv = serve.Server(my_grids, mem_budget=args.mem_budget_gb << 30, tick_iters=8, max_iter=500,
                        stream=stream)
     warm = srv.warm_up()
     reqs = serve.poisson_requests(grids, rate=args.rate, duration=args.serve_seconds,
                                   seed=args.seed + 9)
-    recs, rejected, wall = srv.run(reqs, deadline=2 * args.serve_seconds)
+    my_reqs = [dataclasses.replace(r, grid=local[r.grid]) for r in reqs if r.grid in local]
+    recs, rejected, wall = srv.run(my_reqs, deadline=2 * args.serve_seconds)
     srv.solver.close()
-    recs2, wall2 = serve.serial_baseline(grids, reqs, max_iter=500, stream=stream,
+    recs2, wall2 = serve.serial_baseline(my_grids, my_reqs, max_iter=500, stream=stream,
                                          deadline=2 * args.serve_seconds)
-    return {"pool": len(grids), "resident": len(srv.grid_ids), "resident_bytes": srv.bytes,
+    parts = gather_objects(dict(recs=recs, rejected=len(rejected), wall=wall, recs2=recs2,
+                                wall2=wall2, resident=len(srv.grid_ids), bytes=srv.bytes,
+                                warm=warm, tuned=srv.tuned))
+    all_recs = [r for p in parts for r in p["recs"]]
+    all_recs2 = [r for p in parts for r in p["recs2"]]
+    tuned = parts[0]["tuned"]
+    return {"pool": len(grids), "ranks": ws,
+            "resident": sum(p["resident"] for p in parts),
+            "resident_bytes": sum(p["bytes"] for p in parts),
             "pool_buses": int(sum(sizes)), "rate_per_s": args.rate,
-            "autotuned_branch_blocks": srv.tuned[0] if srv.tuned else None,
-            "autotuned_graph_body_iters": srv.tuned[1] if srv.tuned else None,
-            "arrival_seconds": args.serve_seconds, "pool_cold_solve_s": warm,
-            "served": serve.summarize(recs, wall), "rejected": len(rejected),
-            "serial": serve.summarize(recs2, wall2),
+            "autotuned_branch_blocks": tuned[0] if tuned else None,
+            "autotuned_graph_body_iters": tuned[1] if tuned else None,
+            "arrival_seconds": args.serve_seconds,
+            "pool_cold_solve_s": max(p["warm"] for p in parts),
+            "served": serve.summarize(all_recs, max(p["wall"] for p in parts)),
+            "rejected": sum(p["rejected"] for p in parts),
+            "serial": serve.summarize(all_recs2, max(p["wall2"] for p in parts)),
             "tol": 1e-3, "max_iter_per_request": 500, "tick_iters": 8}
 
 

@@ -27,6 +27,18 @@ def _rank_reduce(rank, world, port, out_dir):
         f.write(f"{t!r} {c['scenarios']!r} {c['converged']!r}\n")
 
 
+def _rank_gather(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    parts = bench.gather_objects({"rank": rank, "recs": list(range(rank + 1))})
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"gather{rank}.txt"), "w") as f:
+        f.write(repr(parts) + "\n")
+
+
 def _rank_main(rank, world, port, times, out_dir):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
@@ -89,3 +101,15 @@ def test_reduce_over_ranks_two_gloo_ranks(tmp_path):
     for rank in range(2):
         t, n, conv = map(float, (tmp_path / f"reduce{rank}.txt").read_text().split())
         assert (t, n, conv) == (5.0, 21.0, 1.0)
+
+
+def test_gather_objects_two_gloo_ranks(tmp_path):
+    pytest.importorskip("torch")
+    import ast
+    import torch.multiprocessing as mp
+    port = _free_port()
+    mp.start_processes(_rank_gather, args=(2, port, str(tmp_path)), nprocs=2,
+                       start_method="spawn", join=True)
+    want = [{"rank": 0, "recs": [0]}, {"rank": 1, "recs": [0, 1]}]
+    for rank in range(2):
+        assert ast.literal_eval((tmp_path / f"gather{rank}.txt").read_text()) == want
