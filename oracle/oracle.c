@@ -412,8 +412,13 @@ static void subspace(const double *x, const double *g, const double *H, const do
  * The initial radius is ||P(x0 - g0) - x0||_2.  The Cauchy search starts from
  * the alpha the branch's previous TRON call ended with (bp->alpha; 1 for the
  * first call) and hands its last alpha back in bp->alpha.
- * A step whose predicted decrease is at most ftol * max(1, |f|) lies below
- * the rounding level of f; the model is trusted for it (ratio taken as 1). */
+ * A step whose predicted decrease is at most ftol * max(1, |f + K|) lies below
+ * the rounding level of f; the model is trusted for it (ratio taken as 1).
+ * K = sum_c y_c^2 / (2 rho_c) turns F into its completed-square form
+ * sum_c rho_c/2 (u_c - t_c)^2 + AL terms, t_c = xbar_c - z_c - y_c/rho_c,
+ * a sum of non-negative terms whose size sets the rounding level of f - ft;
+ * the test is then the same whichever way the constant of eq. branch is
+ * written. */
 int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st)
 {
     const double *lo = bp->lo, *hi = bp->hi;
@@ -428,6 +433,8 @@ int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st
     pstep(x, g, 1.0, lo, hi, sp);
     double delta = nrm2(sp);
     double alpha = bp->alpha > 0.0 ? bp->alpha : 1.0;
+    double K = 0.0;
+    for (int c = 0; c < 8; ++c) K += bp->y[c] * bp->y[c] / (2.0 * bp->rho[c]);
     int status = 1;
     for (int k = 0; k < o->tron_max_iter; ++k) {
         if (pgnorm(x, g, lo, hi) <= gtol) { status = 0; break; }
@@ -450,7 +457,7 @@ int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st
         double actred = f - ft;
         double snorm = nrm2(s);
         if (k == 0 && snorm < delta) delta = snorm;
-        double fa = fabs(f) > 1.0 ? fabs(f) : 1.0;
+        double fa = fabs(f + K) > 1.0 ? fabs(f + K) : 1.0;
         double ratio;
         if (prered <= 0.0) ratio = -1.0;
         else if (prered <= o->tron_ftol * fa) ratio = 1.0;

@@ -838,7 +838,11 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             if (k == 0 && dlt(snorm2, dsq)) dsq = snorm2;
             const double fa = dmaxi(dabsi(f), 1.0);
             // ratio = actred / prered (1 when the model is trusted) against
-            // eta0, eta1, eta2, compared as actred against eta prered (prered > 0)
+            // eta0, eta1, eta2, compared as actred against eta prered (prered > 0).
+            // The model is trusted when prered is below tron_ftol max(1, |f|),
+            // f in its completed-square form sum rho/2 (u - t)^2 + AL terms:
+            // the rounding level of f - ft, whichever way the constant of
+            // eq. branch is written
             const bool trusted = dle(prered, O.tron_ftol * fa);
             const bool below1 = !trusted && dlt(actred, kEta1 * prered);
             const bool above2 = trusted || dlt(kEta2 * prered, actred);
