@@ -8,9 +8,9 @@ in by construction.
 
 This module only *creates inputs*.  It holds none of the ADMM method's
 arithmetic: the operating point that makes each grid feasible is computed from
-circuit laws (branch currents of the pi-model with unit tap, Section II-A), not
-from the solver's admittance or flow routines, and both the CPU oracle and the
-CUDA library receive the arrays built here.
+circuit laws (branch currents of the pi model behind an ideal transformer,
+Section II-A), not from the solver's admittance or flow routines, and both the
+CPU oracle and the CUDA library receive the arrays built here.
 
 Recipe (all draws from one ``numpy.random.Generator(PCG64(seed))``):
 
@@ -20,6 +20,14 @@ Recipe (all draws from one ``numpy.random.Generator(PCG64(seed))``):
   branch count is reached.  Each branch gets a random orientation.
 * Lines: ``r ~ U[0.002, 0.03]``, ``x = r * U[3, 10]``, ``b ~ U[0, 0.05]`` (pu), tap 1,
   shift 0; bus shunts ``gs = bs = 0``; voltage bounds ``[0.94, 1.06]``.
+* Optional devices (``devices=True``; off for the benchmark grids, on in the
+  tests that pin the shunt and transformer terms): 10% of the buses get a shunt
+  ``gs ~ U[0, 0.03]``, ``bs ~ U[-0.1, 0.3]`` (pu at 1 pu voltage), 10% of the
+  branches become transformers with ``tap ~ U[0.95, 1.05]``, and a fifth of
+  those phase shifters with ``shift ~ U[-0.1, 0.1]`` rad.  The feasible point
+  below then accounts for both: flows through an ideal transformer of ratio
+  ``tap e^{j shift}`` at the from end, shunt power ``(gs - j bs) |V|^2`` drawn
+  at the bus.
 * Generators: ``ngen`` distinct random buses; costs ``c2 ~ U[0.01, 0.1]`` $/MW^2h,
   ``c1 ~ U[10, 40]`` $/MWh, ``c0 = 0``.
 * Feasible point: base loads ``pd0 ~ LogNormal(0, 0.8)`` scaled to mean 0.3 pu;
@@ -141,19 +149,26 @@ def _dc_angles(nbus, f, t, x, pinj, ref):
     return th
 
 
-def _branch_power(V, f, t, r, x, b):
+def _branch_power(V, f, t, r, x, b, tap=None, shift=None):
     """Complex power entering each branch at its two ends, from branch currents
-    of the unit-tap pi model (series impedance r + jx, half of b at each end)."""
+    of the pi model (series impedance r + jx, half of b at each end of the
+    series element) behind an ideal transformer of ratio tap e^{j shift} at the
+    from end (tap 1, shift 0 when not given)."""
+    a = np.ones(len(f), dtype=np.complex128)
+    if tap is not None:
+        a = np.where(tap == 0.0, 1.0, tap) * np.exp(1j * (shift if shift is not None else 0.0))
     z = r + 1j * x
-    i_series = (V[f] - V[t]) / z
-    i_f = i_series + 0.5j * b * V[f]
+    vf = V[f] / a                           # from-end voltage behind the transformer
+    i_series = (vf - V[t]) / z
+    i_f = (i_series + 0.5j * b * vf) / np.conj(a)   # the ideal transformer passes S through
     i_t = -i_series + 0.5j * b * V[t]
     return V[f] * np.conj(i_f), V[t] * np.conj(i_t)
 
 
 def make_grid(nbus: int, nbranch: int, ngen: int, seed: int = 0,
-              theta_max: float = 2.0, base_mva: float = 100.0) -> Grid:
-    """Build one seeded synthetic grid with a built-in AC-feasible point."""
+              theta_max: float = 2.0, base_mva: float = 100.0, devices: bool = False) -> Grid:
+    """Build one seeded synthetic grid with a built-in AC-feasible point
+    (``devices``: add bus shunts, transformers and phase shifters)."""
     if not (nbus >= 2 and ngen >= 1 and ngen <= nbus):
         raise ValueError("need nbus >= 2 and 1 <= ngen <= nbus")
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -198,7 +213,21 @@ def make_grid(nbus: int, nbranch: int, ngen: int, seed: int = 0,
     V = vm * np.exp(1j * th)
     qg0 = 0.2 * pg0 * rng.uniform(-1.0, 1.0, ngen)
 
-    s_f, s_t = _branch_power(V, f, t, r, x, b)
+    tap, shift = np.ones(nl), np.zeros(nl)
+    gs, bs = np.zeros(nbus), np.zeros(nbus)
+    if devices:
+        # drawn after every draw of the plain recipe, so the plain grid of a
+        # seed is the same with and without devices up to these
+        d_rng = np.random.Generator(np.random.PCG64(seed + 0x5eed))
+        sh = d_rng.random(nbus) < 0.1
+        gs[sh] = d_rng.uniform(0.0, 0.03, sh.sum())
+        bs[sh] = d_rng.uniform(-0.1, 0.3, sh.sum())
+        tx = d_rng.random(nl) < 0.1
+        tap[tx] = d_rng.uniform(0.95, 1.05, tx.sum())
+        ps = tx & (d_rng.random(nl) < 0.2)
+        shift[ps] = d_rng.uniform(-0.1, 0.1, ps.sum())
+
+    s_f, s_t = _branch_power(V, f, t, r, x, b, tap, shift)
     inj = np.zeros(nbus, dtype=np.complex128)
     np.add.at(inj, f, s_f)
     np.add.at(inj, t, s_t)
@@ -206,8 +235,9 @@ def make_grid(nbus: int, nbranch: int, ngen: int, seed: int = 0,
     gen_q = np.zeros(nbus)
     np.add.at(gen_p, gen_bus, pg0)
     np.add.at(gen_q, gen_bus, qg0)
-    pd = gen_p - inj.real
-    qd = gen_q - inj.imag
+    # balance: generation - load - shunt (gs - j bs)|V|^2 = power into the branches
+    pd = gen_p - inj.real - gs * vm ** 2
+    qd = gen_q - inj.imag + bs * vm ** 2
 
     pmax = pg0 / rng.uniform(0.6, 0.8, ngen)
     pmin = np.zeros(ngen)
@@ -218,26 +248,26 @@ def make_grid(nbus: int, nbranch: int, ngen: int, seed: int = 0,
     f64 = lambda v: np.ascontiguousarray(v, dtype=np.float64)
     return Grid(
         nbus=nbus, nbranch=nl, ngen=ngen, ref_bus=ref, base_mva=base_mva,
-        pd=f64(pd), qd=f64(qd), gs=np.zeros(nbus), bs=np.zeros(nbus),
+        pd=f64(pd), qd=f64(qd), gs=f64(gs), bs=f64(bs),
         vmin=np.full(nbus, 0.94), vmax=np.full(nbus, 1.06),
         f_bus=np.ascontiguousarray(f), t_bus=np.ascontiguousarray(t),
-        r=f64(r), x=f64(x), b=f64(b), tap=np.ones(nl), shift=np.zeros(nl),
+        r=f64(r), x=f64(x), b=f64(b), tap=f64(tap), shift=f64(shift),
         rate_a=f64(rate_a), gen_bus=np.ascontiguousarray(gen_bus),
         pmin=f64(pmin), pmax=f64(pmax), qmin=f64(qmin), qmax=f64(qmax),
         c2=f64(c2), c1=f64(c1), c0=f64(c0),
         vm0=f64(vm), va0=f64(th), pg0=f64(pg0), qg0=f64(qg0), seed=seed)
 
 
-def tiny_grid(seed: int = 0) -> Grid:
+def tiny_grid(seed: int = 0, devices: bool = False) -> Grid:
     """30 buses, 41 branches (29 tree + 12 mesh edges), 6 generators."""
-    return make_grid(30, 41, 6, seed=seed, theta_max=0.2)
+    return make_grid(30, 41, 6, seed=seed, theta_max=0.2, devices=devices)
 
 
-def sized_grid(nbus: int, seed: int = 0) -> Grid:
+def sized_grid(nbus: int, seed: int = 0, devices: bool = False) -> Grid:
     """A grid with the ACTIVSg70k proportions of Table 1 (2k, 10k, 70k buses...)."""
     nl = int(round(BRANCH_RATIO_70K * nbus))
     ng = max(1, int(round(GEN_RATIO_70K * nbus)))
-    return make_grid(nbus, nl, ng, seed=seed, theta_max=2.0)
+    return make_grid(nbus, nl, ng, seed=seed, theta_max=2.0, devices=devices)
 
 
 def penalties_for(nbus: int):

@@ -292,9 +292,15 @@ def test_csr_matches_independent_build(oracle_mod):
     assert np.array_equal(row, exp_row) and np.array_equal(col, exp_col)
 
 
-def test_bus_update_dense_kkt(oracle_mod):
-    """eq. qp-bus: the bus copies solve the dense KKT system of each bus QP."""
-    grid = synth.tiny_grid(1)
+@pytest.mark.parametrize("devices", [False, True])
+def test_bus_update_dense_kkt(oracle_mod, devices):
+    """eq. qp-bus: the bus copies solve the dense KKT system of each bus QP,
+    including the shunt columns (-gs, bs) of w in the balance rows (grids with
+    shunts, transformers and phase shifters: devices=True)."""
+    grid = synth.tiny_grid(1, devices=devices)
+    if devices:
+        assert np.count_nonzero(grid.gs) >= 2 and np.count_nonzero(grid.bs) >= 2
+        assert np.count_nonzero(grid.tap != 1.0) >= 2
     o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4)
     o.solve(tol=0.0, max_iter=7)
     u, z, y, rho = (o.get(k) for k in (oracle_mod.U, oracle_mod.Z, oracle_mod.Y, oracle_mod.RHO))
@@ -409,11 +415,14 @@ def test_one_level_keeps_z_zero(oracle_mod):
 
 
 @pytest.mark.slow
-def test_tiny_admm_solves_acopf(oracle_mod):
+@pytest.mark.parametrize("devices", [False, True])
+def test_tiny_admm_solves_acopf(oracle_mod, devices):
     """Whole method on the 30-bus grid: the converged point satisfies the AC
     power balance to 1e-4 pu and its cost matches an independent NLP solve of
-    eq. acopf to 1e-4 relative; it is no worse than the built-in point."""
-    grid = synth.tiny_grid(0)
+    eq. acopf to 1e-4 relative; it is no worse than the built-in point.  With
+    devices=True the grid has bus shunts (the -gs w and +bs w terms of the
+    balance rows), transformers and phase shifters."""
+    grid = synth.tiny_grid(0, devices=devices)
     o = oracle_mod.Oracle(grid, rho_pq=1e3, rho_va=1e4, beta0=1e5)
     status = o.solve(tol=1e-7, max_iter=20000)
     res = o.residuals()
@@ -445,3 +454,143 @@ def test_ramp_limit_bounds(oracle_mod):
     r = 0.02 * grid.pmax
     assert np.all(pg1 >= np.maximum(grid.pmin, pg0 - r) - 1e-15)
     assert np.all(pg1 <= np.minimum(grid.pmax, pg0 + r) + 1e-15)
+
+
+def _branch_parts_analytic(bp, v):
+    """Objective of eq. branch without the line-limit terms, f0 = sum_c y_c r_c +
+    rho_c/2 r_c^2, and the two squared apparent flows p_e^2 + q_e^2, as
+    functions of v = (v_i, v_j, theta_i, theta_j) written out in real
+    trigonometric form (analytic, so complex steps give exact derivatives)."""
+    gii, bii, gij, bij, gji, bji, gjj, bjj = bp.Y[:]
+    vi, vj, th = v[0], v[1], v[2] - v[3]
+    c, sn = np.cos(th), np.sin(th)
+    u = [gii * vi * vi + vi * vj * (gij * c + bij * sn),
+         -bii * vi * vi + vi * vj * (gij * sn - bij * c),
+         gjj * vj * vj + vi * vj * (gji * c - bji * sn),
+         -bjj * vj * vj + vi * vj * (-gji * sn - bji * c),
+         vi * vi, v[2], vj * vj, v[3]]
+    f0 = 0.0
+    for k in range(8):
+        r = u[k] - bp.xbar[k] + bp.z[k]
+        f0 = f0 + bp.y[k] * r + 0.5 * bp.rho[k] * r * r
+    return f0, [u[0] * u[0] + u[1] * u[1], u[2] * u[2] + u[3] * u[3]]
+
+
+def _cs_grad(fun, v, h=1e-20):
+    return np.array([fun(v + 1j * h * np.eye(len(v))[k]).imag / h for k in range(len(v))])
+
+
+def _kkt_newton(bp, w, lo, hi, rbar2, mu0, iters=30):
+    """Newton's method on the KKT system of min f0 s.t. p_e^2 + q_e^2 <= rbar^2
+    for the active set a starting point shows (limits within 1e-6 of rbar^2,
+    variables at their bounds held there); exact gradients by complex steps,
+    their Jacobian by central differences.  Returns the point, the multipliers
+    of the active limits and the final residual."""
+    f = lambda q: _branch_parts_analytic(bp, q)
+    act = [e for e in range(2) if f(w)[1][e] >= rbar2 - 1e-6]
+    fixed = (w <= lo + 1e-9) | (w >= hi - 1e-9)
+    w = np.where(fixed, np.clip(w, lo, hi), w)
+    fr = np.flatnonzero(~fixed)
+    mu = np.array([mu0[e] for e in act], dtype=float)
+
+    def resid(w, mu):
+        gl = _cs_grad(lambda q: f(q)[0], w)
+        for k, e in enumerate(act):
+            gl = gl + mu[k] * _cs_grad(lambda q, e=e: f(q)[1][e], w)
+        return np.concatenate([gl[fr], [f(w)[1][e] - rbar2 for e in act]])
+
+    n = len(fr) + len(act)
+    for _ in range(iters):
+        r = resid(w, mu)
+        J = np.zeros((n, n))
+        for j in range(n):
+            d = 1e-7
+            wp, wm, mp, mm = w.copy(), w.copy(), mu.copy(), mu.copy()
+            if j < len(fr):
+                wp[fr[j]] += d
+                wm[fr[j]] -= d
+            else:
+                mp[j - len(fr)] += d
+                mm[j - len(fr)] -= d
+            J[:, j] = (resid(wp, mp) - resid(wm, mm)) / (2 * d)
+        step = np.linalg.lstsq(J, -r, rcond=None)[0]
+        w = w.copy()
+        w[fr] += step[:len(fr)]
+        mu = mu + step[len(fr):]
+    return w, dict(zip(act, mu)), np.abs(resid(w, mu)).max()
+
+
+@pytest.mark.parametrize("binding", [True, False])
+def test_branch_al_loop_solves_line_limited_problem(oracle_mod, binding):
+    """Section II-C line limits by the augmented Lagrangian loop around TRON.
+    The loop must return the solution of eq. branch with the line limits
+    imposed exactly, p_e^2 + q_e^2 <= rbar^2 at both ends, and lambda-tilde
+    must be that constraint's KKT multiplier.  Checked two ways, both on an
+    independent restatement with complex-step derivatives: (1) at the loop's
+    point, feasibility to al_tol, stationarity of f0 + sum_e lt_e (p_e^2 +
+    q_e^2) over (v, theta) with the bounds (relative to the gradient at the
+    start, as TRON's own test), lt >= 0 and complementarity; (2)
+    against an independent solve of the constrained problem (slacks
+    eliminated): SciPy SLSQP on the scaled problem from the loop's start and
+    two perturbed starts, each point refined by Newton on its KKT system; the
+    best such point must be the loop's (1e-7), with the same Lagrangian value
+    (the loop stops at |h| <= al_tol, so compare f0 + sum lt h) to 1e-10
+    relative and the same multipliers to 1e-5 relative."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(31 if binding else 37)
+    n_active = 0
+    for it in range(25):
+        bp, x0, _ = _random_prob(oracle_mod, rng, lt=np.zeros(2), rate=0.3 if binding else None)
+        lo, hi = np.array(bp.lo[:]), np.array(bp.hi[:])
+        rbar2 = -lo[4]
+        x, lt, rt, st = oracle_mod.branch_solve(bp, x0)
+        v = x[:4]
+        f0, pq = _branch_parts_analytic(bp, v)
+        # (1) feasibility: h = p^2 + q^2 + s vanishes to al_tol, slack in bounds
+        h = np.array(pq) + x[4:]
+        assert np.abs(h).max() <= 1e-8, (it, h, st)
+        assert np.all(np.array(pq) <= rbar2 + 1e-8)
+        # KKT of  min f0  s.t.  p_e^2 + q_e^2 <= rbar^2, bounds on v
+        gf = _cs_grad(lambda w: _branch_parts_analytic(bp, w)[0], v)
+        gc = [_cs_grad(lambda w, e=e: _branch_parts_analytic(bp, w)[1][e], v) for e in range(2)]
+        G = gf + lt[0] * gc[0] + lt[1] * gc[1]
+        stat = np.abs(np.clip(v - G, lo[:4], hi[:4]) - v).max()
+        g_start = _cs_grad(lambda w: _branch_parts_analytic(bp, w)[0], x0[:4])
+        assert stat <= 1e-9 * max(1.0, np.abs(g_start).max()), (it, stat)
+        scale = max(1.0, np.abs(lt).max())
+        for e in range(2):
+            assert lt[e] >= -1e-9 * scale, (it, lt)
+            active = pq[e] >= rbar2 - 1e-7
+            n_active += active
+            if not active:
+                assert abs(lt[e]) <= 1e-9 * scale, (it, e, lt, pq, rbar2)
+        # (2) the independent solve, objective and limits scaled to order one
+        fs = max(1.0, abs(_branch_parts_analytic(bp, x0[:4])[0]))
+        cons = [{"type": "ineq",
+                 "fun": lambda w, e=e: (rbar2 - _branch_parts_analytic(bp, w)[1][e]) / rbar2,
+                 "jac": lambda w, e=e: -_cs_grad(
+                     lambda q: _branch_parts_analytic(bp, q)[1][e], w) / rbar2}
+                for e in range(2)]
+        best = None
+        for start in [x0[:4]] + [x0[:4] + rng.normal(0, 0.02, 4) for _ in range(2)]:
+            res = minimize(lambda w: _branch_parts_analytic(bp, w)[0] / fs,
+                           np.clip(start, lo[:4], hi[:4]),
+                           jac=lambda w: _cs_grad(lambda q: _branch_parts_analytic(bp, q)[0], w) / fs,
+                           method="SLSQP", bounds=list(zip(lo[:4], hi[:4])), constraints=cons,
+                           options={"ftol": 1e-16, "maxiter": 1000})
+            w, mu, rr = _kkt_newton(bp, res.x, lo[:4], hi[:4], rbar2,
+                                    np.asarray(res.multipliers) * fs / rbar2)
+            fw, pqw = _branch_parts_analytic(bp, w)
+            if (max(pqw) <= rbar2 + 1e-12 and rr <= 1e-12 * max(1.0, np.abs(g_start).max())
+                    and (best is None or fw < best[0])):
+                best = (fw, w, mu)
+        assert best is not None, it
+        fw, w, mu = best
+        assert np.abs(w - v).max() <= 1e-7, (it, w, v)
+        lag = f0 + lt[0] * h[0] + lt[1] * h[1]
+        assert abs(lag - fw) <= 1e-10 * max(1.0, abs(fw)), (it, lag, fw)
+        mscale = max([1.0] + [abs(m) for m in mu.values()])
+        for e in range(2):
+            assert abs(mu.get(e, 0.0) - lt[e]) <= 1e-5 * mscale, (it, mu, lt)
+    if binding:
+        assert n_active >= 10     # the limits do bind in these problems
