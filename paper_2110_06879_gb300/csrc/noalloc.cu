@@ -29,9 +29,10 @@ constexpr int kMaxDevices = 64;
 // the four partial sums of block b.
 static __device__ __align__(256) double g_noalloc_scratch[4 + 4 * kNoallocMaxBlocks];
 
-std::once_flag g_setup_once[kMaxDevices];
+// device address of the scratch array per device, looked up on the first
+// call that succeeds on that device (a failed lookup is retried next call)
+std::mutex g_setup_mutex;
 double *g_scratch_addr[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
 
 __global__ void __launch_bounds__(kNoallocBlock)
 dual_update_noalloc_kernel(double *scratch, long long m, const double *__restrict__ u,
@@ -104,13 +105,16 @@ extern "C" int admm_dual_update_noalloc(int64_t m, const double *d_u, const doub
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADMM_ERR_CUDA;
     // set-up, once per device, with that device current: the device address
     // of the scratch array (its host-side name is only a stand-in)
-    std::call_once(g_setup_once[dev], [dev]() {
-        void *p = nullptr;
-        g_setup_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    });
-    if (g_setup_err[dev] != cudaSuccess || !g_scratch_addr[dev]) return ADMM_ERR_CUDA;
-    double *scratch = g_scratch_addr[dev];
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ADMM_ERR_CUDA;
+            g_scratch_addr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_scratch_addr[dev];
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the ticket counter must start at zero
     if (cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s) != cudaSuccess) return ADMM_ERR_CUDA;
@@ -118,5 +122,7 @@ extern "C" int admm_dual_update_noalloc(int64_t m, const double *d_u, const doub
     dual_update_noalloc_kernel<<<blocks, kNoallocBlock, 0, s>>>(
         scratch, (long long)m, d_u, d_xbar, d_xbar_prev, d_rho, d_lambda, beta, two_level, d_z,
         d_y, d_norms);
-    return cudaGetLastError() == cudaSuccess ? ADMM_OK : ADMM_ERR_CUDA;
+    // the launch's own error only: peeking leaves errors of unrelated earlier
+    // work where their owner will find them
+    return cudaPeekAtLastError() == cudaSuccess ? ADMM_OK : ADMM_ERR_CUDA;
 }
