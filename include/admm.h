@@ -85,13 +85,15 @@ typedef struct {
     double lambda_max;     /* projection bound of the outer multiplier (1e12)        */
     double tol_in0;        /* inner tolerance at outer step k: max(tol, tol_in0 *    */
     double tol_in_decay;   /*   tol_in_decay^k)  (1e-2, 0.5)                         */
-    double al_rho0;        /* initial rho-tilde of a branch solve; <= 0: rho_pq     */
+    double al_rho0;        /* initial rho-tilde of a branch solve; <= 0: rho_pq / (2 rbar)^2,
+                              rbar the tightened rating (rho_pq without a limit)  */
     double al_tol;         /* line-limit AL stops when max|h| <= al_tol (1e-8)       */
     double al_decay;       /* rho-tilde grows unless max|h| fell below this share (0.25) */
-    double al_rho_factor;  /* rho-tilde growth (10)                                  */
+    double al_rho_factor;  /* rho-tilde growth (100)                                 */
     double al_rho_max;     /* cap on rho-tilde (1e12)                                */
     double tron_gtol;      /* TRON: ||P(x-g)-x||_inf <= gtol max(1, start value) (1e-10) */
-    double tron_ftol;      /* TRON: model trusted below ftol max(1,|f|) (1e-12)     */
+    double tron_ftol;      /* TRON: model trusted when the predicted decrease is below
+                              ftol max(1,|f|), f = sum rho/2 (u-t)^2 + AL terms (1e-12) */
     double tron_xtol;      /* TRON: stop on ||s||_inf <= xtol max(1, ||x||_inf) (1e-13) */
     int32_t two_level;     /* 1: two-level algorithm; 0: z == 0 (one level)          */
     int32_t max_outer, max_inner;   /* 20, 1000 (Section IV-A)                        */
@@ -151,7 +153,10 @@ int32_t admm_scenario_count(admm_handle *h);
 int admm_select_scenario(admm_handle *h, int32_t s);
 
 /* Run all device work of this handle on the given cudaStream_t (NULL: the
- * legacy default stream).  The stream must outlive its use by the handle. */
+ * legacy default stream).  The stream must outlive its use by the handle.
+ * Work already queued on the previous stream is ordered before everything
+ * queued on the new one (an event recorded on the old stream, waited on by
+ * the new); the call does not block the host. */
 int admm_set_stream(admm_handle *h, void *cuda_stream);
 
 /* Replace the bus loads (host arrays [nbus]) -- the tracking input of
@@ -253,12 +258,12 @@ int admm_set_state(admm_handle *h, const void *buf, size_t len);
  * bus_dual time, ms_out[2] = mean time of one whole iteration, in ms.  Blocks. */
 int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms_out);
 
-/* Allocation-free z / y update (no counterpart in the paper; it serves
+/* Allocation-free z / y update (the paper has no counterpart; it serves
  * callers).  Some callers cannot call cudaMalloc: a control loop whose device
  * memory is fixed once at start-up, or a program whose device memory all
  * belongs to another allocator and which must not let a library allocate
  * behind its back.  This entry point runs the z update, the y update and the
- * residual reduction of one inner iteration (the z- and y-updates of Algorithm 1) on
+ * residual norms of one inner iteration, elementwise over the m couplings, on
  * buffers the caller owns, and allocates nothing: its only scratch (per-block
  * partial sums and a ticket counter) is a static device array of 128 KiB +
  * 32 B that every GPU loading the library keeps until the process exits.
@@ -300,6 +305,16 @@ int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
  * branch_tron time in ms. */
 int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
                   double *ms_best);
+
+/* Roofline calibration (the paper has no counterpart): one launch of an
+ * FP64-FMA-only kernel (2 blocks of 256 threads per SM, eight independent FMA
+ * chains per thread, `iters` trips) on the given stream (NULL: legacy stream),
+ * timed with CUDA events; blocks until done.  out3[0] = achieved GFLOP/s,
+ * out3[1] = SM clock in MHz during the launch (clock64 cycles over global-timer
+ * nanoseconds on one SM), out3[2] = FMAs per clock per SM sub-partition.
+ * Allocates and frees two small device buffers.  Returns ADMM_OK,
+ * ADMM_ERR_INVALID_ARG (iters < 1, out3 NULL), ADMM_ERR_OOM or ADMM_ERR_CUDA. */
+int admm_fp64_peak(int32_t iters, void *cuda_stream, double *out3);
 
 const char *admm_status_string(int status);
 /* Text of the last error recorded by any call in this process (thread-local). */

@@ -100,7 +100,7 @@ extern "C" void admm_default_options(admm_options *o)
     o->al_rho0 = 0.0;
     o->al_tol = 1e-8;
     o->al_decay = 0.25;
-    o->al_rho_factor = 10.0;
+    o->al_rho_factor = 100.0;
     o->al_rho_max = 1e12;
     o->tron_gtol = 1e-10;
     o->tron_ftol = 1e-12;
@@ -646,7 +646,17 @@ extern "C" int admm_select_scenario(admm_handle *h, int32_t s)
 extern "C" int admm_set_stream(admm_handle *h, void *s)
 {
     if (!h) { set_err("handle is NULL"); return ADMM_ERR_INVALID_ARG; }
-    h->stream = (cudaStream_t)s;
+    cudaStream_t ns = (cudaStream_t)s;
+    if (ns != h->stream) {
+        // order the handle's work queued on the old stream before the new one's
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+        cudaEventDestroy(ev);
+        CK(e);
+    }
+    h->stream = ns;
     return ADMM_OK;
 }
 
