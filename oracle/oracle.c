@@ -482,7 +482,7 @@ int ora_tron(ora_branch_prob *bp, double *x, const ora_options *o, ora_stats *st
 
 /* Augmented Lagrangian loop on p^2 + q^2 + s = 0 of both branch ends
  * (Section II-C; the schedule is this implementation's reading): rho-tilde
- * starts at al_rho0, each pass solves eq. branch by TRON, then
+ * starts at the value the caller sets (bp->rt), each pass solves eq. branch by TRON, then
  * lt += rt h; stop when max|h| <= al_tol, else rt *= al_rho_factor (capped)
  * when max|h| did not fall below al_decay times its previous value.  The
  * Cauchy alpha of each TRON call carries into the next one (bp->alpha). */
@@ -743,6 +743,21 @@ static void update_generators(ora *p)
     }
 }
 
+/* rho-tilde at the start of a branch solve (reading of this implementation;
+ * Section II-C gives no schedule): al_rho0 when set, else
+ * rho_pq / (2 rbar)^2 with rbar the tightened rating, i.e. the penalty
+ * rt/2 h^2 on h = p^2 + q^2 + s weighs a deviation dS of the apparent flow
+ * at the limit (dh = 2 rbar dS) like the coupling penalty rho_pq/2 dS^2
+ * (capped at al_rho_max); rho_pq for a line without a limit. */
+static double al_rho_start(const ora *p, int l)
+{
+    if (p->o.al_rho0 > 0.0) return p->o.al_rho0;
+    double rb2 = -s_lower(p, l);
+    if (!(rb2 < 1e19)) return p->o.rho_pq;
+    double r = p->o.rho_pq / (4.0 * rb2);
+    return r < p->o.al_rho_max ? r : p->o.al_rho_max;
+}
+
 /* Algorithm 1, x-update of the branches: eq. branch by the AL loop around TRON,
  * warm-started from the branch's previous solution clipped to its bounds */
 static void update_branches(ora *p, int l0, int l1)
@@ -756,7 +771,7 @@ static void update_branches(ora *p, int l0, int l1)
             bp.xbar[k] = p->xbar[c]; bp.z[k] = p->z[c]; bp.y[k] = p->y[c]; bp.rho[k] = p->rho[c];
         }
         bp.lt[0] = p->lt[2 * l]; bp.lt[1] = p->lt[2 * l + 1];
-        bp.rt = p->o.al_rho0 > 0.0 ? p->o.al_rho0 : p->o.rho_pq;
+        bp.rt = al_rho_start(p, l);
         bp.alpha = p->balpha[l];
         double *x = &p->bx[6 * l];
         ora_branch_solve(&bp, x, &p->o, &p->st);

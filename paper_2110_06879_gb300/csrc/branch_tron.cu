@@ -765,7 +765,6 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                         b = bb;
                         rpq = sc->rho_pq;
                         rva = sc->rho_va;
-                        rt0 = O.al_rho0 > 0.0 ? O.al_rho0 : rpq;
                         trips = 0;
                         double *my = sh + threadIdx.x;
 #pragma unroll
@@ -779,6 +778,15 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                         B.vhi_j = G.lim[3 * nl + b];
                         B.slo = G.lim[4 * nl + b];
                         B.set_keys();
+                        // rho-tilde starts at rho_pq / (2 rbar)^2: the penalty on
+                        // h = p^2 + q^2 + s weighs a flow deviation at the limit
+                        // like the coupling penalty does (rho_pq without a limit)
+                        {
+                            const double rb2 = -B.slo;
+                            const double r = rpq / (4.0 * rb2);
+                            rt0 = O.al_rho0 > 0.0 ? O.al_rho0
+                                : (rb2 < 1e19 ? (r < O.al_rho_max ? r : O.al_rho_max) : rpq);
+                        }
 #pragma unroll
                         for (int i = 0; i < 6; ++i) x[i] = G.bx[i * nl + b];
                         lt0 = G.blt[b];
