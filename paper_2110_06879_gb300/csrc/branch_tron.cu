@@ -276,11 +276,6 @@ __device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const
     return m;
 }
 
-__device__ __forceinline__ bool cauchy_ok(const double *g, SMat H, const double *s,
-                                          double delta2)
-{
-    return dle(dot6(s, s), delta2) && dle(qmodel(g, H, s), kMu0 * dot6(g, s));
-}
 
 // The loops below (Cauchy trials, Cholesky retries, CG, projected search)
 // have data-dependent trip counts.  They are written warp-uniform: every lane
@@ -296,10 +291,11 @@ __device__ __forceinline__ bool cauchy_ok(const double *g, SMat H, const double 
 // extrapolate by 10 while it holds and the path still moves.  Until the path
 // meets a bound, s(alpha) = -alpha g_P (g_P: g without the components pinned at
 // a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
-// once; trials past a breakpoint evaluate the projection in full.
+// once; trials past a breakpoint evaluate the projection in full.  qsc
+// returns q(s) of the step chosen, from the same closed form or evaluation.
 __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x, const double *g,
                                        SMat H, double d2, double &alpha, double *s,
-                                       Cnt &c)
+                                       double &qsc, Cnt &c)
 {
     bool path[6];
     double room[6], gp[6];
@@ -313,24 +309,28 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
     double hg[6];
     hmul(H, gp, hg);
     const double G2 = dot6(gp, gp), GHG = dot6(gp, hg);
-    // sufficient decrease and radius test at alpha = a (uniform across the warp)
-    auto ok_at = [&](double a, bool need) -> bool {
+    // sufficient decrease and radius test at alpha = a (uniform across the
+    // warp), with q(s(a)) in q
+    auto ok_at = [&](double a, bool need, double &q) -> bool {
         bool unc = true;
 #pragma unroll
         for (int i = 0; i < 6; ++i) unc = unc && (!path[i] || dle(a * dabsi(g[i]), room[i]));
         const double gs = -a * G2;
-        bool ok = dle(a * a * G2, d2) && dle(gs + 0.5 * a * a * GHG, kMu0 * gs);
+        q = gs + 0.5 * a * a * GHG;
+        bool ok = dle(a * a * G2, d2) && dle(q, kMu0 * gs);
         if (__any_sync(kFull, need && !unc)) {
             double t[6];
             pstep(B, x, g, a, t);
-            const bool okf = cauchy_ok(g, H, t, d2);
+            const double qf = qmodel(g, H, t);
+            const bool okf = dle(dot6(t, t), d2) && dle(qf, kMu0 * dot6(g, t));
             ok = unc ? ok : okf;
+            q = unc ? q : qf;
         }
         return ok;
     };
-    double a = alpha;
+    double a = alpha, qa = 0.0;
     if (on) c.cauchy++;
-    const bool back = !ok_at(a, on);
+    const bool back = !ok_at(a, on, qa);
     bool go = on;
     for (int t = 0; t < kCauchyTrials; ++t) {
         if (go && !back) {
@@ -343,11 +343,16 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         if (!__any_sync(kFull, go)) break;
         const double an = back ? a * 0.1 : a * 10.0;
         if (go) c.cauchy++;
-        const bool ok = ok_at(an, go);
-        if (go && (back || ok)) a = an;
+        double qn;
+        const bool ok = ok_at(an, go, qn);
+        if (go && (back || ok)) {
+            a = an;
+            qa = qn;
+        }
         if (ok == back) go = false;    // backtracking found a point / extrapolation failed
     }
     pstep(B, x, g, a, s);
+    qsc = qa;
     if (on) alpha = a;
 }
 
@@ -451,10 +456,11 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
 __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
-                                         SMat H, double d2, const double *sc,
-                                         double *s, double &qs, bool &qs_ok, Cnt &c)
+                                         SMat H, double d2, const double *sc, double qc,
+                                         double *s, double &qs, Cnt &c)
 {
-    qs_ok = false;
+    qs = qc;                 // q(s) for the step returned: the Cauchy point's, or
+                             // the accepted search point's below
     bool fr[6];
     double xc[6];
     bool any = false;
@@ -473,11 +479,14 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
     double L[21], dinv[6];
     precond_factor(act, H, fr, L, dinv);
-    double w[6], r[6], z[6], pv[6], q[6];
+    // hwb: H times the boundary step tau p, which CG adds to w without
+    // updating r; elsewhere H w = r0 - r on the free variables (r0 = -gc)
+    double w[6], r[6], z[6], pv[6], q[6], hwb[6];
     double rn0 = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         w[i] = 0.0;
+        hwb[i] = 0.0;
         r[i] = fr[i] ? -gc[i] : 0.0;
         rn0 += r[i] * r[i];
     }
@@ -517,7 +526,10 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         if (__any_sync(kFull, bnd)) {
             const double tau = boundary_tau(cur, pv, d2);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) w[i] = bnd ? w[i] + tau * pv[i] : w[i];
+            for (int i = 0; i < 6; ++i) {
+                w[i] = bnd ? w[i] + tau * pv[i] : w[i];
+                hwb[i] = bnd ? tau * q[i] : hwb[i];
+            }
         }
         go = go && !bnd;
         double rn = 0.0;
@@ -541,24 +553,47 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
 #pragma unroll
         for (int i = 0; i < 6; ++i) pv[i] = go ? z[i] + be * pv[i] : pv[i];
     }
-    const double qc = qmodel(g, H, sc);
-    qs = qc;                 // q(s) for the step returned: the Cauchy point's, or
-    qs_ok = cgon;            // the accepted search point's below
+    // Projected search along w from the Cauchy point.  While xc + beta w
+    // stays inside the bounds (beta below every free variable's
+    // breakpoint), q(sc + beta w) = q(sc) + beta gc'w + beta^2/2 w'Hw in
+    // closed form, with H w from the CG recurrences; trials past a
+    // breakpoint evaluate the projection in full.
+    double gw = 0.0, whw = 0.0, room[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double hw = fr[i] ? (-gc[i] - r[i]) + hwb[i] : 0.0;
+        gw += gc[i] * w[i];
+        whw += w[i] * hw;
+        room[i] = dpos(w[i]) ? B.hi(i) - xc[i] : xc[i] - B.lo(i);
+    }
     double beta = 1.0;
     bool ps = cgon;
     for (int t = 0; t < kPsTrials; ++t) {
         if (!__any_sync(kFull, ps)) break;
         if (ps) c.ps++;
-        double sb[6], dd[6];
+        bool unc = true;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            sb[i] = B.clamp(i, xc[i] + beta * w[i]) - x[i];
-            dd[i] = sb[i] - sc[i];
+        for (int i = 0; i < 6; ++i) unc = unc && (!fr[i] || dle(beta * dabsi(w[i]), room[i]));
+        const double bgw = beta * gw;
+        double qb = qc + bgw + 0.5 * beta * beta * whw;
+        bool okp = ps && dle(qb, qc + kMu0 * bgw);
+        const bool full = __any_sync(kFull, ps && !unc);
+        if (full || __any_sync(kFull, okp)) {
+            double sb[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sb[i] = B.clamp(i, xc[i] + beta * w[i]) - x[i];
+            if (full) {
+                double dd[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) dd[i] = sb[i] - sc[i];
+                const double qf = qmodel(g, H, sb);
+                const bool okf = ps && dle(qf, qc + kMu0 * dot6(gc, dd));
+                qb = unc ? qb : qf;
+                okp = unc ? okp : okf;
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s[i] = okp ? sb[i] : s[i];
         }
-        const double qb = qmodel(g, H, sb);
-        const bool okp = ps && dle(qb, qc + kMu0 * dot6(gc, dd));
-#pragma unroll
-        for (int i = 0; i < 6; ++i) s[i] = okp ? sb[i] : s[i];
         qs = okp ? qb : qs;
         ps = ps && !okp;
         beta *= 0.5;
@@ -661,15 +696,9 @@ branch_tron_kernel(DevGrid G, DevOpts O)
         }
         if (__any_sync(kFull, go_t)) {
             double sc[6], s[6];
-            double qs = 0.0;
-            bool qs_ok = false;
-            cauchy(go_t, B, x, g, H, dsq, alpha, sc, c);
-            subspace(go_t, B, x, g, H, dsq, sc, s, qs, qs_ok, c);
-            // q(s) is known unless the subspace step stopped at the Cauchy point
-            if (__any_sync(kFull, go_t && !qs_ok)) {
-                const double q2 = qmodel(g, H, s);
-                qs = qs_ok ? qs : q2;
-            }
+            double qs = 0.0, qsc = 0.0;
+            cauchy(go_t, B, x, g, H, dsq, alpha, sc, qsc, c);
+            subspace(go_t, B, x, g, H, dsq, sc, qsc, s, qs, c);
             if (go_t) {
                 double xn = 0.0, sn = 0.0;
 #pragma unroll
