@@ -76,6 +76,7 @@ struct DevGrid {
     // scenario layout: index ranges [off[s], off[s+1]) of each scenario
     const int32_t *bus_off, *br_off, *gen_off, *slot_off, *blk_off;
     const int32_t *blk_scen;       // [nblk_bus] scenario of each bus block
+    const int32_t *blk_bus;        // [nblk_bus + 1] first bus of each bus block (global)
     const int32_t *br_scen;        // [nl] scenario of each branch
     const int32_t *slot_scen;      // [ns] scenario of each incidence slot
     SCtrl *sc;                     // [S]
@@ -129,7 +130,9 @@ __global__ void finalize_kernel(DevGrid G, Range R, double *pg, double *qg, doub
 
 constexpr int kBranchBlock = 128;
 constexpr int kBranchBlocksPerSM = 1;
-constexpr int kBusBlock = 256;
+constexpr int kBusBlock = 256;      // threads of a bus_dual block
+constexpr int kBusPerBlock = 256;   // at most this many buses per bus_dual block
+constexpr int kSlotCap = 768;       // at most this many incidence slots per bus_dual block
 constexpr int kFinBlock = 256;
 
 }  // namespace admm

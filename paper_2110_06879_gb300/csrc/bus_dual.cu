@@ -2,11 +2,15 @@
 // fused into one pass over the bus -> incident-component CSR map, plus the
 // residual reduction and the loop control of the two-level algorithm.
 //
-// One thread owns one bus row.  Every coupling is owned by exactly one bus (the
-// bus its copy lives on), so the gather needs no atomics and sums in CSR order
-// (deterministic).  Generators are owned by their bus too: their closed-form
-// update (eq. qp-bound) uses only the slot values of that row, so it runs in
-// the same thread before the bus update.  The outer multiplier update
+// A block owns a run of consecutive buses (at most kBusPerBlock, at most
+// kSlotCap incidence slots, split on the host) and works in three phases:
+// (A) one thread per slot -- generator updates (eq. qp-bound, the generator's
+// own slot) and every coupling's target u + z + y/rho; (B) one thread per bus
+// -- the row's sums in CSR order from shared memory and the bus closed form;
+// (C) one thread per slot -- bus copies, z, y, residual sums.  Every coupling
+// is owned by exactly one bus (the bus its copy lives on), so the gather needs
+// no atomics and sums in a fixed order (deterministic), and the per-slot
+// phases keep the lanes busy whatever the row lengths.  The outer multiplier update
 // lambda <- Proj(lambda + beta z) is applied lazily: lambda is read only by the
 // z update, so the bus row applies a pending outer update to its slots just
 // before it updates z.  Bus blocks never straddle scenarios (each scenario's
@@ -223,14 +227,21 @@ bus_dual_kernel(DevGrid G, DevOpts O)
 {
     __shared__ double sh[kBusBlock / 32][7];
     __shared__ bool last;
+    // per slot of the block: contributions to its bus's P row, Q row, pooled
+    // w and pooled theta sums, whether it is a branch end, and its bus
+    __shared__ double sA[4][kSlotCap];
+    __shared__ unsigned short sBusOf[kSlotCap];
+    __shared__ unsigned char sIsBr[kSlotCap];
+    // per bus of the block: mu_P, mu_Q, w, theta, w - w_prev, theta - theta_prev
+    __shared__ double sB[6][kBusPerBlock];
     if (G.ctrl->done) return;
     const int sid = G.blk_scen[blockIdx.x];
     SCtrl *c = G.sc + sid;
     if (!c->active || c->done) return;      // this scenario is not iterating
     const int nb = G.nb, nl = G.nl, ng = G.ng, ns = G.ns;
     const int blk0 = G.blk_off[sid], nblk_s = G.blk_off[sid + 1] - blk0;
-    const int i = G.bus_off[sid] + (blockIdx.x - blk0) * blockDim.x + threadIdx.x;
-    const int i_end = G.bus_off[sid + 1];
+    const int i0 = G.blk_bus[blockIdx.x], nbus = G.blk_bus[blockIdx.x + 1] - i0;
+    const int k0 = G.row_ptr[i0], nslot = G.row_ptr[i0 + nbus] - k0;
     const double rpq = c->rho_pq, rva = c->rho_va, beta = c->beta;
     // reciprocals once per block: a division costs about ten FP64 instructions
     const double irpq = 1.0 / rpq, irva = 1.0 / rva;
@@ -238,54 +249,68 @@ bus_dual_kernel(DevGrid G, DevOpts O)
     const bool pending = c->pending != 0;
     const double bused = c->beta_used, lmax = O.lambda_max;
     const bool two = O.two_level != 0;
-    // |u-xbar|^2, |u-xbar+z|^2, |rho dxbar|^2, |z|^2, |u|^2, |xbar|^2, |y|^2
-    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (i < i_end) {
-        const int r0 = G.row_ptr[i], r1 = G.row_ptr[i + 1];
-        const double so = O.obj_scale;
-        // pass 1: generator updates, then the bus QP sums
-        double M00 = 0.0, M11 = 0.0, rP = 0.0, rQ = 0.0;
-        double qw = 0.0, cw = 0.0, qt = 0.0, ct = 0.0;
-        for (int k = r0; k < r1; ++k) {
-            const int e = G.col[k];
-            const double zP = G.sz[k], zQ = G.sz[ns + k], yP = G.sy[k], yQ = G.sy[ns + k];
-            if (e < 2 * nl) {
-                const int l = e >> 1, end = e & 1;
-                const double uP = G.bu[(end ? 2 : 0) * nl + l], uQ = G.bu[(end ? 3 : 1) * nl + l];
-                const double uW = G.bu[(end ? 6 : 4) * nl + l], uT = G.bu[(end ? 7 : 5) * nl + l];
-                const double zW = G.sz[2 * ns + k], zT = G.sz[3 * ns + k];
-                const double yW = G.sy[2 * ns + k], yT = G.sy[3 * ns + k];
-                const double tP = uP + zP + yP * irpq, tQ = uQ + zQ + yQ * irpq;
-                const double tW = uW + zW + yW * irva, tT = uT + zT + yT * irva;
-                M00 += irpq;
-                M11 += irpq;
-                rP -= tP;
-                rQ -= tQ;
-                qw += rva; cw += rva * tW;
-                qt += rva; ct += rva * tT;
-            } else {
-                const int g = e - 2 * nl;
-                // eq. qp-bound: Q = 2 s_o c2' + rho, c = rho (xbar - z) - y - s_o c1'
-                const double xP = G.sx[k], xQ = G.sx[ns + k];
-                double pg = (rpq * (xP - zP) - yP - so * G.gc[ng + g]) / (2.0 * so * G.gc[g] + rpq);
-                double qg = (rpq * (xQ - zQ) - yQ) * irpq;
-                pg = clampd(pg, G.glim[0 * ng + g], G.glim[1 * ng + g]);
-                qg = clampd(qg, G.glim[2 * ng + g], G.glim[3 * ng + g]);
-                G.gu[g] = pg;
-                G.gu[ng + g] = qg;
-                const double tP = pg + zP + yP * irpq, tQ = qg + zQ + yQ * irpq;
-                M00 += irpq;
-                M11 += irpq;
-                rP += tP;
-                rQ += tQ;
-            }
+    const double so = O.obj_scale;
+
+    // (A) one thread per slot: generator updates (eq. qp-bound) and every
+    // coupling's target t = u + z + y/rho, as the slot's share of the bus sums
+    for (int q = threadIdx.x; q < nslot; q += kBusBlock) {
+        const int k = k0 + q;
+        const int e = G.col[k];
+        const double zP = G.sz[k], zQ = G.sz[ns + k], yP = G.sy[k], yQ = G.sy[ns + k];
+        if (e < 2 * nl) {
+            const int l = e >> 1, end = e & 1;
+            const double uP = G.bu[(end ? 2 : 0) * nl + l], uQ = G.bu[(end ? 3 : 1) * nl + l];
+            const double uW = G.bu[(end ? 6 : 4) * nl + l], uT = G.bu[(end ? 7 : 5) * nl + l];
+            const double tW = uW + G.sz[2 * ns + k] + G.sy[2 * ns + k] * irva;
+            const double tT = uT + G.sz[3 * ns + k] + G.sy[3 * ns + k] * irva;
+            sA[0][q] = -(uP + zP + yP * irpq);      // a flow copy enters its row with -1
+            sA[1][q] = -(uQ + zQ + yQ * irpq);
+            sA[2][q] = rva * tW;
+            sA[3][q] = rva * tT;
+            sIsBr[q] = 1;
+        } else {
+            const int g = e - 2 * nl;
+            // eq. qp-bound: Q = 2 s_o c2' + rho, c = rho (xbar - z) - y - s_o c1'
+            const double xP = G.sx[k], xQ = G.sx[ns + k];
+            double pg = (rpq * (xP - zP) - yP - so * G.gc[ng + g]) / (2.0 * so * G.gc[g] + rpq);
+            double qg = (rpq * (xQ - zQ) - yQ) * irpq;
+            pg = clampd(pg, G.glim[0 * ng + g], G.glim[1 * ng + g]);
+            qg = clampd(qg, G.glim[2 * ng + g], G.glim[3 * ng + g]);
+            G.gu[g] = pg;
+            G.gu[ng + g] = qg;
+            sA[0][q] = pg + zP + yP * irpq;
+            sA[1][q] = qg + zQ + yQ * irpq;
+            sA[2][q] = 0.0;
+            sA[3][q] = 0.0;
+            sIsBr[q] = 0;
         }
-        // eq. qp-bus: pooled w (A column (-gs, bs)), then the 2x2 solve
+    }
+    __syncthreads();
+
+    // (B) one thread per bus: the row's sums in CSR order, then eq. qp-bus:
+    // pooled w (A column (-gs, bs)) and the 2x2 solve; theta the pooled target
+    if (threadIdx.x < nbus) {
+        const int i = i0 + threadIdx.x;
+        const int r0 = G.row_ptr[i] - k0, r1 = G.row_ptr[i + 1] - k0;
+        double rP = 0.0, rQ = 0.0, cw = 0.0, ct = 0.0;
+        int nbr = 0;
+        for (int q = r0; q < r1; ++q) {
+            rP += sA[0][q];
+            rQ += sA[1][q];
+            cw += sA[2][q];
+            ct += sA[3][q];
+            nbr += sIsBr[q];
+            sBusOf[q] = (unsigned short)threadIdx.x;
+        }
+        // every copy has weight rho_pq in the P and Q rows (M = A Q^-1 A'),
+        // every branch end weight rho_va in the pooled w and theta
+        const double nrow = (double)(r1 - r0);
+        const double qw = (double)nbr * rva;
         const double gs = G.bus[2 * nb + i], bs = G.bus[3 * nb + i];
         const double iqw = 1.0 / qw;
         const double tw = cw * iqw;
-        M00 += gs * gs * iqw;
-        M11 += bs * bs * iqw;
+        const double M00 = nrow * irpq + gs * gs * iqw;
+        const double M11 = nrow * irpq + bs * bs * iqw;
         const double M01 = -gs * bs * iqw;
         rP += -gs * tw - G.bus[i];
         rQ += bs * tw - G.bus[nb + i];
@@ -294,70 +319,79 @@ bus_dual_kernel(DevGrid G, DevOpts O)
         const double mu0 = (M11 * rP - M01 * rQ) * idet;
         const double mu1 = (M00 * rQ - M01 * rP) * idet;
         const double w = (cw + gs * mu0 - bs * mu1) * iqw;
-        const double th = (i == c->ref) ? 0.0 : ct / qt;
-        const double dw = w - G.bw[i], dth = th - G.bth[i];
+        const double th = (i == c->ref) ? 0.0 : ct / qw;
+        sB[0][threadIdx.x] = mu0;
+        sB[1][threadIdx.x] = mu1;
+        sB[2][threadIdx.x] = w;
+        sB[3][threadIdx.x] = th;
+        sB[4][threadIdx.x] = w - G.bw[i];
+        sB[5][threadIdx.x] = th - G.bth[i];
         G.bw[i] = w;
         G.bth[i] = th;
-        // pass 2: bus copies, lazy outer update, z, y, residuals, branch targets
-        for (int k = r0; k < r1; ++k) {
-            const int e = G.col[k];
-            const bool isb = e < 2 * nl;
-            const int nc = isb ? 4 : 2;
-            const int l = e >> 1, end = e & 1;
-            double u[4], rho[4], irho[4], iz[4];
-            if (isb) {
-                u[0] = G.bu[(end ? 2 : 0) * nl + l];
-                u[1] = G.bu[(end ? 3 : 1) * nl + l];
-                u[2] = G.bu[(end ? 6 : 4) * nl + l];
-                u[3] = G.bu[(end ? 7 : 5) * nl + l];
-            } else {
-                u[0] = G.gu[e - 2 * nl];
-                u[1] = G.gu[ng + e - 2 * nl];
-                u[2] = u[3] = 0.0;
-            }
-            rho[0] = rho[1] = rpq;
-            rho[2] = rho[3] = rva;
-            irho[0] = irho[1] = irpq;
-            irho[2] = irho[3] = irva;
-            iz[0] = iz[1] = izpq;
-            iz[2] = iz[3] = izva;
-            const double sgn = isb ? 1.0 : -1.0;   // A = -1 for flow copies, +1 for generators
+    }
+    __syncthreads();
+
+    // (C) one thread per slot: bus copies, lazy outer update, z, y,
+    // residual sums, branch targets
+    // |u-xbar|^2, |u-xbar+z|^2, |rho dxbar|^2, |z|^2, |u|^2, |xbar|^2, |y|^2
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int q = threadIdx.x; q < nslot; q += kBusBlock) {
+        const int k = k0 + q;
+        const int e = G.col[k];
+        const bool isb = e < 2 * nl;
+        const int nc = isb ? 4 : 2;
+        const int l = e >> 1, end = e & 1;
+        const int bl = sBusOf[q];
+        const double mu0 = sB[0][bl], mu1 = sB[1][bl];
+        double u[4];
+        if (isb) {
+            u[0] = G.bu[(end ? 2 : 0) * nl + l];
+            u[1] = G.bu[(end ? 3 : 1) * nl + l];
+            u[2] = G.bu[(end ? 6 : 4) * nl + l];
+            u[3] = G.bu[(end ? 7 : 5) * nl + l];
+        } else {
+            u[0] = G.gu[e - 2 * nl];
+            u[1] = G.gu[ng + e - 2 * nl];
+            u[2] = u[3] = 0.0;
+        }
+        const double sgn = isb ? 1.0 : -1.0;   // A = -1 for flow copies, +1 for generators
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (c >= nc) break;
-                const double zc = G.sz[c * ns + k], yc = G.sy[c * ns + k];
-                double xb, dual;
-                if (c < 2) {
-                    const double tc = u[c] + zc + yc * irho[c];
-                    xb = tc + sgn * (c == 0 ? mu0 : mu1) * irho[c];
-                    dual = rho[c] * (xb - G.sx[c * ns + k]);
-                    G.sx[c * ns + k] = xb;
-                } else {
-                    xb = c == 2 ? w : th;
-                    dual = rho[c] * (c == 2 ? dw : dth);
-                }
-                double lc = G.sl[c * ns + k];
-                if (pending) {
-                    lc = clampd(lc + bused * zc, -lmax, lmax);
-                    G.sl[c * ns + k] = lc;
-                }
-                const double r0c = u[c] - xb;
-                const double zn = two ? -(lc + yc + rho[c] * r0c) * iz[c] : 0.0;
-                const double yn = yc + rho[c] * (r0c + zn);
-                G.sz[c * ns + k] = zn;
-                G.sy[c * ns + k] = yn;
-                acc[0] += r0c * r0c;
-                acc[1] += (r0c + zn) * (r0c + zn);
-                acc[2] += dual * dual;
-                acc[3] += zn * zn;
-                acc[4] += u[c] * u[c];
-                acc[5] += xb * xb;
-                acc[6] += yn * yn;
-                if (isb) {
-                    // component index in bt: from end {0,1,4,5}, to end {2,3,6,7}
-                    const int comp = (c < 2 ? c : c + 2) + (end ? 2 : 0);
-                    G.bt[comp * nl + l] = xb - zn - yn * irho[c];
-                }
+        for (int cc = 0; cc < 4; ++cc) {
+            if (cc >= nc) break;
+            const bool pq = cc < 2;
+            const double rho = pq ? rpq : rva, irho = pq ? irpq : irva, iz = pq ? izpq : izva;
+            const double zc = G.sz[cc * ns + k], yc = G.sy[cc * ns + k];
+            double xb, dual;
+            if (pq) {
+                const double tc = u[cc] + zc + yc * irho;
+                xb = tc + sgn * (cc == 0 ? mu0 : mu1) * irho;
+                dual = rho * (xb - G.sx[cc * ns + k]);
+                G.sx[cc * ns + k] = xb;
+            } else {
+                xb = sB[cc == 2 ? 2 : 3][bl];
+                dual = rho * sB[cc == 2 ? 4 : 5][bl];
+            }
+            double lc = G.sl[cc * ns + k];
+            if (pending) {
+                lc = clampd(lc + bused * zc, -lmax, lmax);
+                G.sl[cc * ns + k] = lc;
+            }
+            const double r0c = u[cc] - xb;
+            const double zn = two ? -(lc + yc + rho * r0c) * iz : 0.0;
+            const double yn = yc + rho * (r0c + zn);
+            G.sz[cc * ns + k] = zn;
+            G.sy[cc * ns + k] = yn;
+            acc[0] += r0c * r0c;
+            acc[1] += (r0c + zn) * (r0c + zn);
+            acc[2] += dual * dual;
+            acc[3] += zn * zn;
+            acc[4] += u[cc] * u[cc];
+            acc[5] += xb * xb;
+            acc[6] += yn * yn;
+            if (isb) {
+                // component index in bt: from end {0,1,4,5}, to end {2,3,6,7}
+                const int comp = (cc < 2 ? cc : cc + 2) + (end ? 2 : 0);
+                G.bt[comp * nl + l] = xb - zn - yn * irho;
             }
         }
     }
