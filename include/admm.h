@@ -252,6 +252,24 @@ int admm_get_stats(admm_handle *h, int64_t *out9);
 int admm_get_state(admm_handle *h, void *buf, size_t *len);
 int admm_set_state(admm_handle *h, const void *buf, size_t len);
 
+/* One scenario's iteration state as an opaque host blob (paging a grid out
+ * of a handle and back into this or another handle that holds the same grid
+ * as one of its scenarios): the same arrays as admm_get_state, restricted to
+ * scenario s, and its outer penalty and pending outer step.  Inputs (loads,
+ * generator bounds) are not part of it.  Call with buf == NULL to get the
+ * size in *len.  admm_set_scenario_state accepts a blob of the same shape
+ * (bus, branch, generator and slot counts) only for a scenario that is not
+ * running; a following warm start of that scenario continues the saved
+ * trajectory bitwise.  Both synchronise the handle's stream. */
+int admm_get_scenario_state(admm_handle *h, int32_t s, void *buf, size_t *len);
+int admm_set_scenario_state(admm_handle *h, int32_t s, const void *buf, size_t len);
+
+/* Device bytes admm_create_batch would allocate for these grids (the one
+ * state allocation of the handle; the iteration graph and the CUDA context
+ * come on top), without touching the device: what a server admits against a
+ * device-memory budget.  Only the sizes of the grids are read. */
+int admm_device_bytes(const admm_grid *grids, int32_t nscen, size_t *bytes);
+
 /* Tracing: run `iters` inner iterations from the current state (warm, no
  * convergence stop) with stream launches and CUDA events around each kernel on
  * the handle's stream; ms_out[0] = mean branch_tron time, ms_out[1] = mean

@@ -93,6 +93,10 @@ def lib():
             "admm_autotune": (C.c_int, [vp, i32, vp, vp, vp]),
             "admm_dual_update_noalloc": (C.c_int, [C.c_int64, vp, vp, vp, vp, vp, d, i32, vp, vp,
                                                    vp, vp]),
+            "admm_fp64_peak": (C.c_int, [i32, vp, vp]),
+            "admm_get_scenario_state": (C.c_int, [vp, i32, vp, C.POINTER(C.c_size_t)]),
+            "admm_set_scenario_state": (C.c_int, [vp, i32, vp, C.c_size_t]),
+            "admm_device_bytes": (C.c_int, [C.POINTER(admm_grid), i32, C.POINTER(C.c_size_t)]),
             "admm_status_string": (C.c_char_p, [C.c_int]),
             "admm_last_error": (C.c_char_p, []),
         }
@@ -102,6 +106,26 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def fp64_peak(iters=20000, stream=None) -> dict:
+    """FP64 FMA-only calibration launch (admm_fp64_peak): achieved GFLOP/s,
+    the SM clock in MHz during it, FMAs per clock per SM sub-partition."""
+    out = np.zeros(3)
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().admm_fp64_peak(iters, C.c_void_p(raw or 0), _ptr(out)), "admm_fp64_peak")
+    return dict(gflops=float(out[0]), sm_mhz=float(out[1]), fma_per_clk_smsp=float(out[2]))
+
+
+def device_bytes(grids) -> int:
+    """Device bytes a handle over `grids` (one grid or a list) allocates for
+    its state (admm_device_bytes)."""
+    grids = list(grids) if isinstance(grids, (list, tuple)) else [grids]
+    keep = []
+    arr = (admm_grid * len(grids))(*[_grid_struct(g, keep) for g in grids])
+    n = C.c_size_t(0)
+    _check(lib().admm_device_bytes(arr, len(grids), C.byref(n)), "admm_device_bytes")
+    return int(n.value)
 
 
 def _ptr(a):
@@ -314,3 +338,14 @@ class Solver:
     def set_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib().admm_set_state(self.h, buf, len(blob)), "admm_set_state")
+
+    def get_scenario_state(self, s: int) -> bytes:
+        n = C.c_size_t(0)
+        _check(lib().admm_get_scenario_state(self.h, s, None, C.byref(n)), "admm_get_scenario_state")
+        buf = C.create_string_buffer(n.value)
+        _check(lib().admm_get_scenario_state(self.h, s, buf, C.byref(n)), "admm_get_scenario_state")
+        return buf.raw[: n.value]
+
+    def set_scenario_state(self, s: int, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().admm_set_scenario_state(self.h, s, buf, len(blob)), "admm_set_scenario_state")

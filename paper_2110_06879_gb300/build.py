@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libadmm.so")
-SOURCES = ["branch_tron.cu", "bus_dual.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["branch_tron.cu", "bus_dual.cu", "capi.cu", "noalloc.cu", "calibrate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

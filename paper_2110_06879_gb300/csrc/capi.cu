@@ -171,8 +171,14 @@ int validate(const admm_grid *g, const admm_options *o)
         if (g->r[l] == 0.0 && g->x[l] == 0.0) { set_err("branch %d has zero impedance", l); return ADMM_ERR_INVALID_ARG; }
         deg[f]++; deg[t]++;
     }
+    for (int k = 0; k < g->ngen; ++k)
+        if (g->gen_bus[k] >= 0 && g->gen_bus[k] < g->nbus) deg[g->gen_bus[k]]++;
     for (int i = 0; i < g->nbus; ++i) {
         if (deg[i] == 0) { set_err("bus %d has no incident branch", i); return ADMM_ERR_INVALID_ARG; }
+        if (deg[i] > kSlotCap) {
+            set_err("bus %d has %d incident branch ends and generators (at most %d)", i, deg[i], kSlotCap);
+            return ADMM_ERR_INVALID_ARG;
+        }
         if (!(g->vmin[i] > 0.0) || g->vmin[i] > g->vmax[i]) { set_err("bus %d: need 0 < vmin <= vmax", i); return ADMM_ERR_INVALID_ARG; }
     }
     for (int k = 0; k < g->ngen; ++k) {
@@ -206,6 +212,94 @@ struct Carver {
         return o;
     }
 };
+
+// Offsets of every device array in the handle's single allocation.
+struct Layout {
+    size_t fb, tb, Y, lim, bx, blt, bt, bu, raw, balpha, gb, gc, glim, gu, gbase, bus, bw, bth,
+        rp, col, sx, sz, sy, sl, cls, part, fpart, hist, ctrl, sc, offs, blks, brs, sls, out, blkb;
+    size_t bytes;
+};
+
+// Sizes of one handle: totals over its scenarios, bus blocks (bus_dual) and
+// finalize blocks, the largest scenario (output staging).
+struct Sizes {
+    long long nb = 0, nl = 0, ng = 0, ns = 0;
+    int S = 0, nblk_bus = 0, nblk_fin = 1, maxnb = 1, maxnl = 1, maxng = 1;
+};
+
+// Bus blocks of bus_dual for one grid: consecutive buses, at most
+// kBusPerBlock of them and at most kSlotCap incidence slots (branch ends and
+// generators) per block.  Returns the block count; `starts` (if given)
+// receives the first bus (local index) of each block.  Needs every bus's
+// slot count <= kSlotCap (checked in validate).
+int bus_block_starts(const admm_grid &g, std::vector<int32_t> *starts)
+{
+    std::vector<int> deg(g.nbus, 0);
+    for (int l = 0; l < g.nbranch; ++l) { deg[g.f_bus[l]]++; deg[g.t_bus[l]]++; }
+    for (int k = 0; k < g.ngen; ++k) deg[g.gen_bus[k]]++;
+    int n = 0, i = 0;
+    while (i < g.nbus) {
+        if (starts) starts->push_back(i);
+        int cnt = 0, slots = 0;
+        while (i < g.nbus && cnt < kBusPerBlock && slots + deg[i] <= kSlotCap) {
+            slots += deg[i];
+            ++cnt;
+            ++i;
+        }
+        ++n;
+    }
+    return n;
+}
+
+Sizes sizes_of(const admm_grid *grids, int S)
+{
+    Sizes z;
+    z.S = S;
+    for (int s = 0; s < S; ++s) {
+        const admm_grid &g = grids[s];
+        z.nb += g.nbus; z.nl += g.nbranch; z.ng += g.ngen;
+        z.nblk_bus += bus_block_starts(g, nullptr);
+        const int nf = (g.nbus + g.nbranch + g.ngen + kFinBlock - 1) / kFinBlock;
+        z.nblk_fin = nf > z.nblk_fin ? nf : z.nblk_fin;
+        z.maxnb = g.nbus > z.maxnb ? g.nbus : z.maxnb;
+        z.maxnl = g.nbranch > z.maxnl ? g.nbranch : z.maxnl;
+        z.maxng = g.ngen > z.maxng ? g.ngen : z.maxng;
+    }
+    z.ns = 2 * z.nl + z.ng;
+    return z;
+}
+
+Layout layout_of(const Sizes &z)
+{
+    const size_t nb = z.nb, nl = z.nl, ng = z.ng, ns = z.ns, S = z.S;
+    Carver cv;
+    Layout L;
+    L.fb = cv.take<int32_t>(nl); L.tb = cv.take<int32_t>(nl);
+    L.Y = cv.take<double>(8 * nl); L.lim = cv.take<double>(5 * nl);
+    L.bx = cv.take<double>(6 * nl); L.blt = cv.take<double>(2 * nl);
+    L.bt = cv.take<double>(8 * nl); L.bu = cv.take<double>(8 * nl);
+    L.raw = cv.take<double>(6 * nl);
+    L.balpha = cv.take<double>(nl);
+    L.gb = cv.take<int32_t>(ng > 0 ? ng : 1);
+    L.gc = cv.take<double>(3 * ng + 1); L.glim = cv.take<double>(4 * ng + 1);
+    L.gu = cv.take<double>(2 * ng + 1);
+    L.gbase = cv.take<double>(2 * ng + 1);
+    L.bus = cv.take<double>(6 * nb); L.bw = cv.take<double>(nb); L.bth = cv.take<double>(nb);
+    L.rp = cv.take<int32_t>(nb + 1); L.col = cv.take<int32_t>(ns);
+    L.sx = cv.take<double>(2 * ns); L.sz = cv.take<double>(4 * ns);
+    L.sy = cv.take<double>(4 * ns); L.sl = cv.take<double>(4 * ns);
+    L.cls = cv.take<int32_t>(2 * (size_t)kClasses * nl);
+    L.part = cv.take<double>(8 * (size_t)z.nblk_bus); L.fpart = cv.take<double>(2 * (size_t)z.nblk_fin);
+    L.hist = cv.take<double>(4 * (size_t)kHistCap);
+    L.ctrl = cv.take<Ctrl>(1);
+    L.sc = cv.take<SCtrl>(S);
+    L.offs = cv.take<int32_t>(5 * (S + 1));
+    L.blks = cv.take<int32_t>(z.nblk_bus); L.brs = cv.take<int32_t>(nl); L.sls = cv.take<int32_t>(ns);
+    L.blkb = cv.take<int32_t>(z.nblk_bus + 1);
+    L.out = cv.take<double>(2 * (size_t)z.maxnb + 4 * (size_t)z.maxnl + 2 * (size_t)z.maxng + 1);
+    L.bytes = cv.off;
+    return L;
+}
 
 int launch_check(const char *what)
 {
@@ -406,7 +500,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
         h->bus_off[s + 1] = h->bus_off[s] + grids[s].nbus;
         h->br_off[s + 1] = h->br_off[s] + grids[s].nbranch;
         h->gen_off[s + 1] = h->gen_off[s] + grids[s].ngen;
-        h->blk_off[s + 1] = h->blk_off[s] + (grids[s].nbus + kBusBlock - 1) / kBusBlock;
+        h->blk_off[s + 1] = h->blk_off[s] + bus_block_starts(grids[s], nullptr);
         h->base_mva[s] = grids[s].base_mva;
     }
     // concatenated topology in global indices
@@ -422,6 +516,15 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
         for (int k = 0; k < g.ngen; ++k) h->gen_bus[h->gen_off[s] + k] = h->bus_off[s] + g.gen_bus[k];
         for (int b = h->blk_off[s]; b < h->blk_off[s + 1]; ++b) blk_scen[b] = s;
     }
+    // first bus (global) of every bus_dual block, and the end
+    std::vector<int32_t> blk_bus;
+    blk_bus.reserve(h->blk_off[S] + 1);
+    for (int s = 0; s < S; ++s) {
+        std::vector<int32_t> st;
+        bus_block_starts(grids[s], &st);
+        for (int32_t b : st) blk_bus.push_back(h->bus_off[s] + b);
+    }
+    blk_bus.push_back(h->bus_off[S]);
     // CSR bus -> incident entries by a stable counting sort over entry ids
     h->row_ptr.assign(nb + 1, 0);
     h->col.assign(ns, 0);
@@ -447,44 +550,12 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
         h->nblk_branch = need < cap ? need : cap;
     }
     h->nblk_bus = h->blk_off[S];
-    int maxfin = 1;
-    for (int s = 0; s < S; ++s) {
-        const int n = (grids[s].nbus + grids[s].nbranch + grids[s].ngen + kFinBlock - 1) / kFinBlock;
-        maxfin = n > maxfin ? n : maxfin;
-    }
-    h->nblk_fin = maxfin;
+    const Sizes zs = sizes_of(grids, S);
+    h->nblk_fin = zs.nblk_fin;
     h->nblk_flush = (4 * ns + 255) / 256 < 1184 ? (4 * ns + 255) / 256 : 1184;
     // device layout
-    Carver cv;
-    size_t o_fb = cv.take<int32_t>(nl), o_tb = cv.take<int32_t>(nl);
-    size_t o_Y = cv.take<double>(8 * (size_t)nl), o_lim = cv.take<double>(5 * (size_t)nl);
-    size_t o_bx = cv.take<double>(6 * (size_t)nl), o_blt = cv.take<double>(2 * (size_t)nl);
-    size_t o_bt = cv.take<double>(8 * (size_t)nl), o_bu = cv.take<double>(8 * (size_t)nl);
-    size_t o_raw = cv.take<double>(6 * (size_t)nl);
-    size_t o_balpha = cv.take<double>(nl);
-    size_t o_gb = cv.take<int32_t>(ng > 0 ? ng : 1);
-    size_t o_gc = cv.take<double>(3 * (size_t)ng + 1), o_glim = cv.take<double>(4 * (size_t)ng + 1);
-    size_t o_gu = cv.take<double>(2 * (size_t)ng + 1);
-    size_t o_gbase = cv.take<double>(2 * (size_t)ng + 1);
-    size_t o_bus = cv.take<double>(6 * (size_t)nb), o_bw = cv.take<double>(nb), o_bth = cv.take<double>(nb);
-    size_t o_rp = cv.take<int32_t>(nb + 1), o_col = cv.take<int32_t>(ns);
-    size_t o_sx = cv.take<double>(2 * (size_t)ns), o_sz = cv.take<double>(4 * (size_t)ns);
-    size_t o_sy = cv.take<double>(4 * (size_t)ns), o_sl = cv.take<double>(4 * (size_t)ns);
-    size_t o_cls = cv.take<int32_t>(2 * (size_t)kClasses * nl);
-    size_t o_part = cv.take<double>(8 * (size_t)h->nblk_bus), o_fpart = cv.take<double>(2 * (size_t)h->nblk_fin);
-    size_t o_hist = cv.take<double>(4 * (size_t)kHistCap);
-    size_t o_ctrl = cv.take<Ctrl>(1);
-    size_t o_sc = cv.take<SCtrl>(S);
-    size_t o_offs = cv.take<int32_t>(5 * (size_t)(S + 1));
-    size_t o_blks = cv.take<int32_t>(h->nblk_bus), o_brs = cv.take<int32_t>(nl), o_sls = cv.take<int32_t>(ns);
-    int maxnb = 1, maxnl = 1, maxng = 1;
-    for (int s = 0; s < S; ++s) {
-        maxnb = grids[s].nbus > maxnb ? grids[s].nbus : maxnb;
-        maxnl = grids[s].nbranch > maxnl ? grids[s].nbranch : maxnl;
-        maxng = grids[s].ngen > maxng ? grids[s].ngen : maxng;
-    }
-    size_t o_out = cv.take<double>(2 * (size_t)maxnb + 4 * (size_t)maxnl + 2 * (size_t)maxng + 1);
-    h->dbytes = cv.off;
+    const Layout Lo = layout_of(zs);
+    h->dbytes = Lo.bytes;
     cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
     if (e != cudaSuccess) {
         set_err("cudaMalloc(%zu) failed: %s", h->dbytes, cudaGetErrorString(e));
@@ -502,31 +573,32 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     G.nb = nb; G.nl = nl; G.ng = ng; G.ns = ns; G.S = S;
     G.nblk_bus = h->nblk_bus;
     G.nblk_branch = h->nblk_branch;
-    G.f_bus = (int32_t *)(base + o_fb); G.t_bus = (int32_t *)(base + o_tb);
-    G.Y = (double *)(base + o_Y); G.lim = (double *)(base + o_lim);
-    G.bx = (double *)(base + o_bx); G.blt = (double *)(base + o_blt);
-    G.bt = (double *)(base + o_bt); G.bu = (double *)(base + o_bu);
-    G.raw = (double *)(base + o_raw);
-    G.balpha = (double *)(base + o_balpha);
-    G.gen_bus = (int32_t *)(base + o_gb);
-    G.gc = (double *)(base + o_gc); G.glim = (double *)(base + o_glim); G.gu = (double *)(base + o_gu);
-    G.gbase = (double *)(base + o_gbase);
-    G.bus = (double *)(base + o_bus); G.bw = (double *)(base + o_bw); G.bth = (double *)(base + o_bth);
-    G.row_ptr = (int32_t *)(base + o_rp); G.col = (int32_t *)(base + o_col);
-    G.sx = (double *)(base + o_sx); G.sz = (double *)(base + o_sz);
-    G.sy = (double *)(base + o_sy); G.sl = (double *)(base + o_sl);
-    G.cls_list = (int32_t *)(base + o_cls);
-    G.partials = (double *)(base + o_part); G.fin_partials = (double *)(base + o_fpart);
-    G.hist = (double *)(base + o_hist);
-    G.ctrl = (Ctrl *)(base + o_ctrl);
-    G.sc = (SCtrl *)(base + o_sc);
-    int32_t *offs = (int32_t *)(base + o_offs);
+    G.f_bus = (int32_t *)(base + Lo.fb); G.t_bus = (int32_t *)(base + Lo.tb);
+    G.Y = (double *)(base + Lo.Y); G.lim = (double *)(base + Lo.lim);
+    G.bx = (double *)(base + Lo.bx); G.blt = (double *)(base + Lo.blt);
+    G.bt = (double *)(base + Lo.bt); G.bu = (double *)(base + Lo.bu);
+    G.raw = (double *)(base + Lo.raw);
+    G.balpha = (double *)(base + Lo.balpha);
+    G.gen_bus = (int32_t *)(base + Lo.gb);
+    G.gc = (double *)(base + Lo.gc); G.glim = (double *)(base + Lo.glim); G.gu = (double *)(base + Lo.gu);
+    G.gbase = (double *)(base + Lo.gbase);
+    G.bus = (double *)(base + Lo.bus); G.bw = (double *)(base + Lo.bw); G.bth = (double *)(base + Lo.bth);
+    G.row_ptr = (int32_t *)(base + Lo.rp); G.col = (int32_t *)(base + Lo.col);
+    G.sx = (double *)(base + Lo.sx); G.sz = (double *)(base + Lo.sz);
+    G.sy = (double *)(base + Lo.sy); G.sl = (double *)(base + Lo.sl);
+    G.cls_list = (int32_t *)(base + Lo.cls);
+    G.partials = (double *)(base + Lo.part); G.fin_partials = (double *)(base + Lo.fpart);
+    G.hist = (double *)(base + Lo.hist);
+    G.ctrl = (Ctrl *)(base + Lo.ctrl);
+    G.sc = (SCtrl *)(base + Lo.sc);
+    int32_t *offs = (int32_t *)(base + Lo.offs);
     G.bus_off = offs; G.br_off = offs + (S + 1); G.gen_off = offs + 2 * (S + 1);
     G.slot_off = offs + 3 * (S + 1); G.blk_off = offs + 4 * (S + 1);
-    G.blk_scen = (int32_t *)(base + o_blks); G.br_scen = (int32_t *)(base + o_brs);
-    G.slot_scen = (int32_t *)(base + o_sls);
+    G.blk_scen = (int32_t *)(base + Lo.blks); G.br_scen = (int32_t *)(base + Lo.brs);
+    G.slot_scen = (int32_t *)(base + Lo.sls);
+    G.blk_bus = (int32_t *)(base + Lo.blkb);
     G.line_limit_frac = op.line_limit_frac;
-    h->dout = (double *)(base + o_out);
+    h->dout = (double *)(base + Lo.out);
     DevOpts &O = h->O;
     O.obj_scale = op.obj_scale;
     O.beta0 = op.beta0; O.beta_factor = op.beta_factor; O.z_decay = op.z_decay;
@@ -587,6 +659,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
             !up((void *)G.row_ptr, h->row_ptr.data(), (nb + 1) * 4) || !up((void *)G.col, h->col.data(), ns * 4) ||
             !up(G.sc, sc.data(), sizeof(SCtrl) * S) || !up(offs, offv.data(), offv.size() * 4) ||
             !up((void *)G.blk_scen, blk_scen.data(), blk_scen.size() * 4) ||
+            !up((void *)G.blk_bus, blk_bus.data(), blk_bus.size() * 4) ||
             !up((void *)G.br_scen, br_scen.data(), br_scen.size() * 4) ||
             !up((void *)G.slot_scen, slot_scen.data(), slot_scen.size() * 4)) {
             set_err("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -613,6 +686,18 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
         return ADMM_ERR_CUDA;
     }
     *out = h;
+    return ADMM_OK;
+}
+
+extern "C" int admm_device_bytes(const admm_grid *grids, int32_t nscen, size_t *bytes)
+{
+    if (!grids || nscen < 1 || !bytes) { set_err("need grids, nscen >= 1 and bytes"); return ADMM_ERR_INVALID_ARG; }
+    for (int s = 0; s < nscen; ++s)
+        if (grids[s].nbus < 1 || grids[s].nbranch < 1 || grids[s].ngen < 0) {
+            set_err("scenario %d: need nbus >= 1, nbranch >= 1, ngen >= 0", s);
+            return ADMM_ERR_INVALID_ARG;
+        }
+    *bytes = layout_of(sizes_of(grids, nscen)).bytes;
     return ADMM_OK;
 }
 
@@ -970,8 +1055,123 @@ std::vector<StatePart> state_parts(admm_handle *h)
 }
 
 constexpr int kScalarsPerScenario = 4;   // beta, total iterations, beta_used, pending
+constexpr uint64_t kScenMagic = 0x41444d4d53433031ull;   // "ADMMSC01"
+
+// The same arrays by index space, for the state of one scenario: rows of
+// length nl (branches), ng (generators), nb (buses) or ns (slots).
+enum Space { SP_BR = 0, SP_GEN, SP_BUS, SP_SLOT };
+struct ScenPart {
+    double *dev;
+    int rows;
+    Space sp;
+};
+
+std::vector<ScenPart> scenario_parts(admm_handle *h)
+{
+    const DevGrid &G = h->G;
+    return {{G.bx, 6, SP_BR},   {G.blt, 2, SP_BR},   {G.bt, 8, SP_BR},   {G.bu, 8, SP_BR},
+            {G.gu, 2, SP_GEN},  {G.bw, 1, SP_BUS},   {G.bth, 1, SP_BUS}, {G.sx, 2, SP_SLOT},
+            {G.sz, 4, SP_SLOT}, {G.sy, 4, SP_SLOT},  {G.sl, 4, SP_SLOT}, {G.balpha, 1, SP_BR}};
+}
+
+// [offset, count) of scenario s and the row stride in each index space
+void scen_range(const admm_handle *h, int s, Space sp, size_t &off, size_t &cnt, size_t &stride)
+{
+    const std::vector<int32_t> &o = sp == SP_BR ? h->br_off : sp == SP_GEN ? h->gen_off
+                                  : sp == SP_BUS ? h->bus_off : h->slot_off;
+    off = (size_t)o[s];
+    cnt = (size_t)(o[s + 1] - o[s]);
+    stride = sp == SP_BR ? h->nl : sp == SP_GEN ? h->ng : sp == SP_BUS ? h->nb : h->ns;
+}
+
+size_t scen_blob_bytes(admm_handle *h, int s)
+{
+    size_t n = 0;
+    for (auto &p : scenario_parts(h)) {
+        size_t off, cnt, stride;
+        scen_range(h, s, p.sp, off, cnt, stride);
+        n += (size_t)p.rows * cnt;
+    }
+    return 6 * sizeof(uint64_t) + kScalarsPerScenario * sizeof(double) + n * sizeof(double);
+}
 
 }  // namespace
+
+extern "C" int admm_get_scenario_state(admm_handle *h, int32_t s, void *buf, size_t *len)
+{
+    NvtxRange nvtx_("admm_get_scenario_state");
+    if (!h || !len || s < 0 || s >= h->S) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    const size_t need = scen_blob_bytes(h, s);
+    if (!buf) { *len = need; return ADMM_OK; }
+    if (*len < need) { set_err("state buffer too small (%zu < %zu)", *len, need); return ADMM_ERR_INVALID_ARG; }
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
+    uint64_t *hdr = (uint64_t *)buf;
+    hdr[0] = kScenMagic;
+    hdr[1] = (uint64_t)(h->bus_off[s + 1] - h->bus_off[s]);
+    hdr[2] = (uint64_t)(h->br_off[s + 1] - h->br_off[s]);
+    hdr[3] = (uint64_t)(h->gen_off[s + 1] - h->gen_off[s]);
+    hdr[4] = (uint64_t)(h->slot_off[s + 1] - h->slot_off[s]);
+    hdr[5] = 0;
+    double *sc = (double *)(hdr + 6);
+    const SCtrl &c = h->hsc[s];
+    sc[0] = c.beta;
+    sc[1] = (double)c.total_iters;
+    sc[2] = c.pending ? c.beta_used : 0.0;
+    sc[3] = (double)c.pending;
+    double *p = sc + kScalarsPerScenario;
+    for (auto &pt : scenario_parts(h)) {
+        size_t off, cnt, stride;
+        scen_range(h, s, pt.sp, off, cnt, stride);
+        for (int r = 0; r < pt.rows; ++r) {
+            if (cnt)
+                CK(cudaMemcpyAsync(p, pt.dev + r * stride + off, cnt * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->stream));
+            p += cnt;
+        }
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    *len = need;
+    return ADMM_OK;
+}
+
+extern "C" int admm_set_scenario_state(admm_handle *h, int32_t s, const void *buf, size_t len)
+{
+    NvtxRange nvtx_("admm_set_scenario_state");
+    if (!h || !buf || s < 0 || s >= h->S) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
+    const uint64_t *hdr = (const uint64_t *)buf;
+    if (len != scen_blob_bytes(h, s) || len < 6 * sizeof(uint64_t) || hdr[0] != kScenMagic ||
+        hdr[1] != (uint64_t)(h->bus_off[s + 1] - h->bus_off[s]) ||
+        hdr[2] != (uint64_t)(h->br_off[s + 1] - h->br_off[s]) ||
+        hdr[3] != (uint64_t)(h->gen_off[s + 1] - h->gen_off[s]) ||
+        hdr[4] != (uint64_t)(h->slot_off[s + 1] - h->slot_off[s])) {
+        set_err("scenario state blob does not match scenario %d of this handle", s);
+        return ADMM_ERR_INVALID_ARG;
+    }
+    int rc = sync_sc(h);
+    if (rc != ADMM_OK) return rc;
+    SCtrl &c = h->hsc[s];
+    if (c.active && !c.done) { set_err("scenario %d is running", s); return ADMM_ERR_INVALID_ARG; }
+    const double *sc = (const double *)(hdr + 6);
+    c.beta = sc[0];
+    c.total_iters = (int32_t)sc[1];
+    c.beta_used = sc[2];
+    c.pending = (int32_t)sc[3];
+    const double *p = sc + kScalarsPerScenario;
+    for (auto &pt : scenario_parts(h)) {
+        size_t off, cnt, stride;
+        scen_range(h, s, pt.sp, off, cnt, stride);
+        for (int r = 0; r < pt.rows; ++r) {
+            if (cnt)
+                CK(cudaMemcpyAsync(pt.dev + r * stride + off, p, cnt * sizeof(double),
+                                   cudaMemcpyHostToDevice, h->stream));
+            p += cnt;
+        }
+    }
+    CK(cudaMemcpyAsync(h->G.sc + s, &c, sizeof(SCtrl), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADMM_OK;
+}
 
 extern "C" int admm_get_state(admm_handle *h, void *buf, size_t *len)
 {
