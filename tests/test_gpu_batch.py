@@ -5,7 +5,9 @@ solo trajectories."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2110_06879_gb300 import admm, synth
+from parity import compare_state
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +54,39 @@ def test_batch_equals_solo_bitwise():
     # scenarios stopped independently (per-scenario convergence mask)
     st_all, it_all = b.slot_status()
     assert list(it_all) == iters
+
+
+def test_batched_scenarios_match_oracle():
+    """Each scenario of a mixed batch against an oracle run of the same grid
+    and inputs at 1e-9: scenarios of different sizes (one with shunts and
+    transformers) begun at different times -- two join while others are
+    iterating -- and one restarted warm with new loads after it stopped."""
+    grids = [synth.tiny_grid(10), synth.sized_grid(600, seed=3),
+             synth.tiny_grid(11, devices=True), synth.sized_grid(300, seed=4)]
+    b = admm.Solver(grids, **TINY)
+    b.slot_begin(0, tol=0.0, max_iter=10)
+    b.slot_begin(1, tol=0.0, max_iter=8)
+    b.run(4)
+    b.slot_begin(2, tol=0.0, max_iter=6)              # joins mid-run
+    b.run(3)
+    b.slot_begin(3, tol=0.0, max_iter=9)              # joins later still
+    b.run(100)
+    pd1, qd1 = grids[1].pd * 1.03, grids[1].qd * 0.98
+    b.select(1)
+    b.set_loads(pd1, qd1)
+    b.slot_begin(1, tol=0.0, max_iter=5, warm_start=True)   # warm restart, new loads
+    b.run(50)
+    st, it = b.slot_status()
+    assert list(it) == [10, 5, 6, 9]
+    for k, (g, n) in enumerate(zip(grids, (10, 8, 6, 9))):
+        o = oracle.Oracle(g, **TINY)
+        o.solve(tol=0.0, max_iter=n)
+        if k == 1:
+            o.set_loads(pd1, qd1)
+            o.solve(tol=0.0, max_iter=5, warm_start=True)
+        b.select(k)
+        compare_state(b, o, 1e-9, f"scenario {k}")
+    b.close()
 
 
 def test_continuous_batching_slots_follow_solo_trajectories():
