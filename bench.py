@@ -60,8 +60,8 @@ def algorithmic_flops(stats: dict) -> float:
 # aside) is the one the counters were taken on; any change to it makes the
 # figure stale (null).
 TRAFFIC_CAPTURE = {"nbus": 70000, "seed": 1,
-                   "source_digest": "8db3e3afe68cf8237b39fea213029f90db37222bcad02a0876dbd5d5ff2c6f78",
-                   "bytes_per_launch": 22.223616e6 + 0.548352e6}
+                   "source_digest": "89b7d6b2b497c785018e414c1989d43647a243b7d3bfc0921cf1b3da7ad4f969",
+                   "bytes_per_launch": 22.303744e6 + 0.549376e6}
 
 
 def kernel_source_digest(path):
@@ -89,11 +89,39 @@ def branch_tron_traffic(args):
     return c["bytes_per_launch"]
 
 
-def fp64_peak_gflops():
-    """FP64 peak of a GB300 from unit counts and clock: 152 SMs x 4 sub-
-    partitions x 0.5 FP64 FMA per clock (one warp instruction per 64 cycles
-    per sub-partition, measured) x 2 flops x 2.07 GHz = 1,258.6 GFLOP/s."""
-    return 152 * 4 * 0.5 * 2 * 2.070
+def fp64_peak_gflops(fma_per_clk_smsp=0.5, sm_mhz=2070.0, sms=152):
+    """FP64 peak from unit counts and clock: SMs x 4 sub-partitions x FP64 FMAs
+    per clock per sub-partition (0.5 on GB300: one warp instruction per 64
+    cycles; measured live by admm_fp64_peak) x 2 flops x the SM clock
+    (152 x 4 x 0.5 x 2 x 2.07 GHz = 1,258.6 GFLOP/s)."""
+    return sms * 4 * fma_per_clk_smsp * 2 * sm_mhz / 1e3
+
+
+def bus_dual_work(grid):
+    """Algorithmic work of one bus_dual launch (one inner iteration's
+    generator, bus, z and y updates and residual sums), from the closed forms:
+    FP64 flops (an FMA counts 2) and compulsory DRAM bytes.
+      per branch-end coupling 36 flops: target u + z + y/rho (3), bus sums
+        (2.5), bus copy (2.5), dual residual (2), u - xbar (1), z (4), y (3),
+        seven squared norms (15), branch target xbar - z - y/rho (3);
+      per generator coupling 41 (the closed-form generator update instead of
+        the branch target); per bus 30 (pooled w, 2x2 solve, theta);
+      bytes per branch end 228 (reads u, z, y 4 each, sx 2, col; writes z, y 4
+        each, sx 2, targets 4), per generator 164, per bus 68."""
+    nb, nl, ng = grid.nbus, grid.nbranch, grid.ngen
+    flops = 36 * 8 * nl + 41 * 2 * ng + 30 * nb
+    nbytes = 228 * 2 * nl + 164 * ng + 68 * nb
+    return flops, nbytes
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json, driver-written),
+    else the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json"), encoding="utf-8") as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 class ClockSampler:
@@ -232,6 +260,65 @@ def workload_config(grid, opts, args):
             "l2": "flushed (256 MiB write) between timed steps", "parallelism": "replicas"}
 
 
+STOP_RULE = ("standard ADMM test (Boyd et al. 2011, Sec. 3.3.1), absolute and relative tolerance "
+             "both tol: ||u - xbar||_2 <= sqrt(m) tol + tol max(||u||_2, ||xbar||_2), "
+             "||rho (xbar - xbar_prev)||_2 <= sqrt(m) tol + tol ||y||_2, and ||z||_2 <= the "
+             "first bound (two-level); m couplings")
+
+
+def solve_timed(s, stream, tol, max_iter, warm):
+    """One admm_solve (a single graph launch) timed with CUDA events on the
+    handle's stream, with the residual norms, the objective and ||c(x)||_inf of
+    the point it returns."""
+    import torch
+    from paper_2110_06879_gb300 import admm
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.solve_async(tol=tol, max_iter=max_iter, warm_start=warm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    r = s.residuals()
+    sol = s.solution()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    return {"tol": tol, "warm_start": bool(warm), "seconds": secs, "iters": r["iters"],
+            "iters_per_s": r["iters"] / secs if secs > 0 else None,
+            "outer_iters": r["outer_iters"],
+            "status": admm.lib().admm_status_string(r["status"]).decode(),
+            "primal": r["primal"], "eps_pri": r["eps_pri"], "dual": r["dual"],
+            "eps_dual": r["eps_dual"], "z_norm": r["z_norm"], "objective": sol["objective"],
+            "max_viol": sol["max_viol"], "stop_rule": STOP_RULE}
+
+
+def time_to_violation(s, stream, target, max_iter, chunk):
+    """Cold start, then `chunk` iterations at a time (one graph launch each)
+    until ||c(x)||_inf of the current point (flows recomputed from the bus
+    voltages; power balance, line limits at the full rating, voltage bounds)
+    is at most `target`, or max_iter iterations.  The timed region includes the
+    evaluation of ||c(x)||_inf after every chunk."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    s.slot_begin(0, tol=0.0, max_iter=max_iter, warm_start=False)
+    it, sol, best = 0, None, None
+    while it < max_iter:
+        s.run(chunk)
+        sol = s.solution()
+        it = int(s.slot_status()[1][0])
+        if best is None or sol["max_viol"] < best[1]:
+            best = (it, sol["max_viol"])
+        if sol["max_viol"] <= target:
+            break
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    reached = sol["max_viol"] <= target
+    return {"target_max_viol": target, "reached": bool(reached), "seconds": secs, "iters": it,
+            "max_viol": sol["max_viol"], "objective": sol["objective"],
+            "best_max_viol": best[1], "best_at_iter": best[0], "check_every": chunk,
+            "max_iter": max_iter}
+
+
 def shard_scenarios(sizes, ws, rank):
     """Indices of the scenarios rank `rank` of `ws` solves: longest first onto
     the least-loaded rank (load = buses), ties to the lower rank; disjoint,
@@ -322,10 +409,11 @@ def gather_objects(obj):
 
 def run_served(args, admm, stream):
     """Continuous batching over a resident pool (log-uniform 1k-70k buses, one
-    grid pinned at 70k) under Poisson load-snapshot requests, against the same
-    stream served by serial plain solves.  With several ranks the pool is
-    sharded like the batched scenarios and each rank serves the requests for
-    its own grids; the records are gathered once at the end."""
+    grid pinned at 70k) under Poisson load-snapshot requests at each rate of
+    --rates, against the same streams served by serial plain solves.  With
+    several ranks the pool is sharded like the batched scenarios and each rank
+    serves the requests for its own grids; the records are gathered once per
+    rate at the end."""
     import dataclasses
     import numpy as np
     from paper_2110_06879_gb300 import serve, synth
@@ -340,30 +428,68 @@ def run_served(args, admm, stream):
     srv = serve.Server(my_grids, mem_budget=args.mem_budget_gb << 30, tick_iters=8, max_iter=500,
                        stream=stream)
     warm = srv.warm_up()
-    reqs = serve.poisson_requests(grids, rate=args.rate, duration=args.serve_seconds,
-                                  seed=args.seed + 9)
-    my_reqs = [dataclasses.replace(r, grid=local[r.grid]) for r in reqs if r.grid in local]
-    recs, rejected, wall = srv.run(my_reqs, deadline=2 * args.serve_seconds)
+    serial_solvers = {}
+    per_rate = []
+    for q, rate in enumerate(args.rates):
+        duration = min(args.serve_seconds, args.max_requests / rate)
+        deadline = duration + args.grace_seconds
+        reqs = serve.poisson_requests(grids, rate=rate, duration=duration,
+                                      seed=args.seed + 9 + 101 * q)
+        my_reqs = [dataclasses.replace(r, grid=local[r.grid]) for r in reqs if r.grid in local]
+        recs, rejected, wall = srv.run(my_reqs, deadline=deadline)
+        recs2, wall2 = serve.serial_baseline(my_grids, my_reqs, max_iter=500, stream=stream,
+                                             deadline=deadline, solvers=serial_solvers)
+        parts = gather_objects(dict(recs=recs, rejected=len(rejected), wall=wall, recs2=recs2,
+                                    wall2=wall2))
+        all_recs = [r for p in parts for r in p["recs"]]
+        all_recs2 = [r for p in parts for r in p["recs2"]]
+        per_rate.append({"rate_per_s": rate, "arrival_seconds": duration,
+                         "no_admission_after_s": deadline,
+                         "served": serve.summarize(all_recs, max(p["wall"] for p in parts)),
+                         "rejected": sum(p["rejected"] for p in parts),
+                         "serial": serve.summarize(all_recs2, max(p["wall2"] for p in parts))})
+    # the same pool under a device-memory budget that holds about half of it:
+    # grids are swapped in as requests for them arrive (idle ones evicted,
+    # least recently used first, their states kept on the host)
+    limited = None
+    if args.limited_share > 0:
+        states = srv.saved_states()
+        budget = int(args.limited_share * serve.state_bytes(my_grids))
+        srv2 = serve.Server(my_grids, mem_budget=budget, tick_iters=8, max_iter=500, stream=stream,
+                            states=states, tuned=srv.tuned)
+        rate = args.rates[0]
+        duration = min(args.serve_seconds, args.max_requests / rate)
+        reqs = serve.poisson_requests(grids, rate=rate, duration=duration, seed=args.seed + 77)
+        my_reqs = [dataclasses.replace(r, grid=local[r.grid]) for r in reqs if r.grid in local]
+        resident0 = len(srv2.grid_ids)
+        recs, rejected, wall = srv2.run(my_reqs, deadline=duration + args.grace_seconds)
+        parts = gather_objects(dict(recs=recs, rejected=len(rejected), wall=wall,
+                                    swaps=srv2.swaps, evictions=srv2.evictions, budget=budget,
+                                    resident0=resident0))
+        limited = {"rate_per_s": rate, "arrival_seconds": duration,
+                   "budget_bytes": sum(p["budget"] for p in parts),
+                   "budget_share_of_pool": args.limited_share,
+                   "initially_resident": sum(p["resident0"] for p in parts),
+                   "swaps": sum(p["swaps"] for p in parts),
+                   "evictions": sum(p["evictions"] for p in parts),
+                   "served": serve.summarize([r for p in parts for r in p["recs"]],
+                                             max(p["wall"] for p in parts)),
+                   "rejected": sum(p["rejected"] for p in parts)}
+        srv2.solver.close()
     srv.solver.close()
-    recs2, wall2 = serve.serial_baseline(my_grids, my_reqs, max_iter=500, stream=stream,
-                                         deadline=2 * args.serve_seconds)
-    parts = gather_objects(dict(recs=recs, rejected=len(rejected), wall=wall, recs2=recs2,
-                                wall2=wall2, resident=len(srv.grid_ids), bytes=srv.bytes,
-                                warm=warm, tuned=srv.tuned))
-    all_recs = [r for p in parts for r in p["recs"]]
-    all_recs2 = [r for p in parts for r in p["recs2"]]
-    tuned = parts[0]["tuned"]
+    for sv in serial_solvers.values():
+        sv.close()
+    info = gather_objects(dict(resident=len(srv.grid_ids), bytes=srv.bytes, warm=warm,
+                               tuned=srv.tuned))
+    tuned = info[0]["tuned"]
     return {"pool": len(grids), "ranks": ws,
-            "resident": sum(p["resident"] for p in parts),
-            "resident_bytes": sum(p["bytes"] for p in parts),
-            "pool_buses": int(sum(sizes)), "rate_per_s": args.rate,
+            "resident": sum(p["resident"] for p in info),
+            "resident_bytes": sum(p["bytes"] for p in info),
+            "pool_buses": int(sum(sizes)),
             "autotuned_branch_blocks": tuned[0] if tuned else None,
             "autotuned_graph_body_iters": tuned[1] if tuned else None,
-            "arrival_seconds": args.serve_seconds,
-            "pool_cold_solve_s": max(p["warm"] for p in parts),
-            "served": serve.summarize(all_recs, max(p["wall"] for p in parts)),
-            "rejected": sum(p["rejected"] for p in parts),
-            "serial": serve.summarize(all_recs2, max(p["wall2"] for p in parts)),
+            "pool_cold_solve_s": max(p["warm"] for p in info),
+            "rates": per_rate, "memory_limited": limited,
             "tol": 1e-3, "max_iter_per_request": 500, "tick_iters": 8}
 
 
@@ -416,11 +542,20 @@ def run_ours(args):
     clocks = clk.summary()
     value, t_total = whole_job_rate(sum(iter_ms) / 1e3, args.steps, device=dev)
 
-    # dominant kernel roofline (FP64 ALU bound)
+    # dominant kernel roofline (FP64 ALU bound): the peak from the FP64 rate
+    # per clock measured live by the calibration kernel, at the SM clock the
+    # timed region ran at
+    cal = admm.fp64_peak(20000, stream)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_gflops(cal["fma_per_clk_smsp"], mhz, sms)
     b_mean = sum(branch_ms) / len(branch_ms)
     flops_per_launch = algorithmic_flops(stats_acc) / args.steps
     achieved = flops_per_launch / (b_mean * 1e-3) / 1e9
-    peak = fp64_peak_gflops()
+    u_mean = sum(bus_ms) / len(bus_ms)
+    bd_flops, bd_bytes = bus_dual_work(grid)
+    bd_achieved = bd_flops / (u_mean * 1e-3) / 1e9
+    hbm_peak = measured_hbm_gbs()
 
     # end to end through the public API with host buffers, over the same
     # iterations (state restored to the end of the warm-up)
@@ -438,43 +573,86 @@ def run_ours(args):
            "h2d_bytes_per_step": int(pd.nbytes + qd.nbytes),
            "d2h_bytes_per_step": C_RESIDUALS_BYTES}
 
-    # time to residual 1e-3 from a cold start (whole solve, one graph launch)
-    tt = None
+    # time to residual 1e-3 from a cold start (whole solve, one graph launch),
+    # then warm after one AR(1) load step (Section IV-C)
+    tt = tt_warm = None
     if args.time_to_tol:
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        s.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        r = s.residuals()
-        sol = s.solution()
-        secs = ev0.elapsed_time(ev1) / 1e3
-        tt = {"tol": 1e-3, "seconds": secs, "iters": r["iters"], "iters_per_s": r["iters"] / secs,
-              "outer_iters": r["outer_iters"],
-              "status": admm.lib().admm_status_string(r["status"]).decode(),
-              "primal": r["primal"], "eps_pri": r["eps_pri"], "dual": r["dual"],
-              "eps_dual": r["eps_dual"], "z_norm": r["z_norm"],
-              "objective": sol["objective"], "max_viol": sol["max_viol"],
-              "graph_launches": 1}
+        tt = solve_timed(s, stream, 1e-3, args.tol_max_iter, False)
+        tt["graph_launches"] = 1
+        from paper_2110_06879_gb300 import synth
+        pd1, qd1 = synth.ar1_loads(grid, 1, seed=args.seed + 400 + rank)
+        s.set_loads(pd1[0], qd1[0])
+        tt_warm = solve_timed(s, stream, 1e-3, args.tol_max_iter, True)
+        tt_warm["load_step"] = "one AR(1) step, phi 0.9, 1% noise per bus"
+        s.set_loads(grid.pd, grid.qd)
+
+    # time to a usable point: ||c(x)||_inf <= 1.5e-2 (Table 2's level at 70k)
+    feas = None
+    if args.feasible:
+        fs = admm.Solver(grid, stream=stream, **dict(opts, rho_pq=args.feas_rho[0],
+                                                     rho_va=args.feas_rho[1]))
+        feas = time_to_violation(fs, stream, args.feas_target, args.feas_max_iter, 100)
+        feas.update({"rho_pq": args.feas_rho[0], "rho_va": args.feas_rho[1]})
+        fs.close()
 
     # the one-level variant (z = 0, Mhanna et al.) on the same grid, as a speed
     # comparison: time to the same tolerance from a cold start
     tt1 = None
     if args.time_to_tol and args.one_level:
         s1 = admm.Solver(grid, stream=stream, two_level=0, **opts)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        s1.solve_async(tol=1e-3, max_iter=args.tol_max_iter, warm_start=False)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        r = s1.residuals()
-        sol = s1.solution()
-        secs = ev0.elapsed_time(ev1) / 1e3
-        tt1 = {"tol": 1e-3, "seconds": secs, "iters": r["iters"], "iters_per_s": r["iters"] / secs,
-               "status": admm.lib().admm_status_string(r["status"]).decode(),
-               "primal": r["primal"], "dual": r["dual"], "objective": sol["objective"],
-               "max_viol": sol["max_viol"]}
+        tt1 = solve_timed(s1, stream, 1e-3, args.tol_max_iter, False)
         s1.close()
+
+    # smaller grids of the same kind (2k, 10k): time to 1e-3 and to the
+    # violation target, and the 2k objective against the oracle's own solve
+    sizes = None
+    if args.sizes:
+        from paper_2110_06879_gb300 import synth
+        sizes = []
+        for nb in args.sizes:
+            g2 = synth.sized_grid(nb, seed=args.seed + rank)
+            o2 = dict(rho_pq=args.size_rho[0], rho_va=args.size_rho[1], obj_scale=1.0)
+            s2 = admm.Solver(g2, stream=stream, **o2)
+            rec = {"nbus": nb, "nbranch": g2.nbranch, "ngen": g2.ngen,
+                   "rho_pq": o2["rho_pq"], "rho_va": o2["rho_va"],
+                   "time_to_tol": solve_timed(s2, stream, 1e-3, args.tol_max_iter, False)}
+            s2.close()
+            if args.feasible:
+                s3 = admm.Solver(g2, stream=stream, **dict(o2, rho_pq=args.feas_rho[0],
+                                                          rho_va=args.feas_rho[1]))
+                rec["time_to_max_viol"] = time_to_violation(s3, stream, args.feas_target,
+                                                            args.feas_max_iter, 100)
+                rec["time_to_max_viol"].update({"rho_pq": args.feas_rho[0],
+                                                "rho_va": args.feas_rho[1]})
+                s3.close()
+                # the one-level variant (z = 0) at its own penalties
+                s4 = admm.Solver(g2, stream=stream, two_level=0,
+                                 **dict(o2, rho_pq=args.feas_rho1[0], rho_va=args.feas_rho1[1]))
+                rec["time_to_max_viol_one_level"] = time_to_violation(
+                    s4, stream, args.feas_target, args.feas_max_iter, 100)
+                rec["time_to_max_viol_one_level"].update({"rho_pq": args.feas_rho1[0],
+                                                          "rho_va": args.feas_rho1[1]})
+                s4.close()
+            gpu_iters = rec["time_to_tol"]["iters"]
+            if rank == 0 and nb <= args.gap_max_nbus and gpu_iters > args.gap_max_iter:
+                rec["oracle"] = {"skipped": f"the GPU solve took {gpu_iters} iterations; the "
+                                            f"oracle leg runs at most {args.gap_max_iter}"}
+            elif rank == 0 and nb <= args.gap_max_nbus:
+                # the oracle's own solve of the same problem, at most as many
+                # iterations as the GPU took (the trajectories agree, so both
+                # stop on the same iteration)
+                import oracle
+                oo = oracle.Oracle(g2, **o2)
+                t0 = time.perf_counter()
+                st = oo.solve(tol=1e-3, max_iter=gpu_iters)
+                osec = time.perf_counter() - t0
+                of = oo.finalize()
+                og = rec["time_to_tol"]["objective"]
+                rec["oracle"] = {"status": int(st), "iters": oo.residuals()["iters"],
+                                 "seconds_1core": osec, "objective": of["objective"],
+                                 "max_viol": of["max_viol"],
+                                 "objective_gap_rel": abs(og - of["objective"]) / abs(of["objective"])}
+            sizes.append(rec)
 
     # warm-start tracking: 10k-bus grid, AR(1) load snapshots, renewable ramps,
     # 2% ramp limit, each snapshot warm-started (Section IV-C)
@@ -492,7 +670,8 @@ def run_ours(args):
         track.update({"workload": f"synthetic {tgrid.nbus}-bus grid ({tgrid.nbranch} branches, "
                                   f"{tgrid.ngen} generators), AR(1) loads phi 0.9 noise 1%, 20% "
                                   "renewable p_max ramps +-3%, ramp limit 2% p_max, warm starts",
-                      "rho_pq": topts["rho_pq"], "rho_va": topts["rho_va"], "tol": 1e-3})
+                      "rho_pq": topts["rho_pq"], "rho_va": topts["rho_va"], "tol": 1e-3,
+                      "stop_rule": STOP_RULE})
         ts.close()
 
     batched = run_batched(args, admm, stream, device=dev) if args.batched > 0 else None
@@ -507,15 +686,33 @@ def run_ours(args):
                              "peak": peak, "unit": "GFLOP/s (FP64)", "frac": achieved / peak,
                              "traffic": branch_tron_traffic(args), "traffic_unit": "bytes",
                              "ms_per_launch": b_mean,
-                             "flops_per_launch": flops_per_launch},
-                "bus_dual_ms": sum(bus_ms) / len(bus_ms),
+                             "flops_per_launch": flops_per_launch,
+                             "peak_source": "SMs x 4 x measured FP64 FMA/clk per sub-partition "
+                                            "x 2 x max SM clock sampled in the timed region"},
+                "roofline_bus_dual": {"kernel": "bus_dual", "bound": "alu", "achieved": bd_achieved,
+                                      "peak": peak, "unit": "GFLOP/s (FP64)",
+                                      "frac": bd_achieved / peak, "ms_per_launch": u_mean,
+                                      "flops_per_launch": bd_flops,
+                                      "bytes_per_launch": bd_bytes,
+                                      "achieved_gbs": bd_bytes / (u_mean * 1e-3) / 1e9,
+                                      "hbm_peak_gbs": hbm_peak,
+                                      "hbm_frac": (bd_bytes / (u_mean * 1e-3) / 1e9 / hbm_peak)
+                                      if hbm_peak else None},
+                "fp64_calibration": cal,
+                "bus_dual_ms": u_mean,
                 "branch_solves_per_s": value * grid.nbranch,
                 "e2e": e2e, "clocks": clocks, "gpu_launches": LAUNCHES_PER_STEP * args.steps * ws,
                 "tron_stats_per_step": {k: v / args.steps for k, v in stats_acc.items()}}
         if tt is not None:
             line["time_to_tol"] = tt
+        if tt_warm is not None:
+            line["time_to_tol_warm"] = tt_warm
+        if feas is not None:
+            line["time_to_max_viol"] = feas
         if tt1 is not None:
             line["time_to_tol_one_level"] = tt1
+        if sizes is not None:
+            line["grids"] = sizes
         if track is not None:
             line["tracking"] = track
         if batched is not None:
@@ -535,7 +732,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nbus", type=int, default=70000)
@@ -544,17 +741,39 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-time-to-tol", dest="time_to_tol", action="store_false")
     ap.add_argument("--tol-max-iter", type=int, default=5000)
+    ap.add_argument("--no-feasible", dest="feasible", action="store_false",
+                    help="skip the time-to-||c(x)||_inf legs")
+    ap.add_argument("--feas-target", type=float, default=1.5e-2)
+    ap.add_argument("--feas-max-iter", type=int, default=12000)
+    ap.add_argument("--feas-rho", type=float, nargs=2, default=[3e4, 3e6])
+    ap.add_argument("--feas-rho1", type=float, nargs=2, default=[1e4, 1e6],
+                    help="penalties of the one-level time-to-violation leg on the smaller grids")
+    ap.add_argument("--sizes", type=int, nargs="*", default=[2000, 10000],
+                    help="smaller grids timed to 1e-3 and to the violation target")
+    ap.add_argument("--size-rho", type=float, nargs=2, default=[3e3, 3e4])
+    ap.add_argument("--gap-max-nbus", type=int, default=2000,
+                    help="largest grid whose objective is compared with an oracle solve")
+    ap.add_argument("--gap-max-iter", type=int, default=1500,
+                    help="longest GPU solve (iterations) the oracle comparison repeats")
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
     ap.add_argument("--no-one-level", dest="one_level", action="store_false",
                     help="skip the one-level (z = 0) time-to-tolerance comparison")
-    ap.add_argument("--batched", type=int, default=0,
-                    help="add the batched leg with this many scenarios (256 in the workload)")
+    ap.add_argument("--batched", type=int, default=256,
+                    help="scenarios of the batched leg (0 skips it)")
     ap.add_argument("--batch-sample", type=int, default=8)
-    ap.add_argument("--served", action="store_true", help="add the continuous-batching leg")
+    ap.add_argument("--no-served", dest="served", action="store_false",
+                    help="skip the continuous-batching leg")
     ap.add_argument("--pool", type=int, default=32)
-    ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--rates", type=float, nargs="+", default=[50.0, 200.0, 2000.0])
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="longest arrival window per rate")
+    ap.add_argument("--max-requests", type=int, default=300,
+                    help="arrival window per rate is at most this many mean arrivals")
+    ap.add_argument("--grace-seconds", type=float, default=3.0,
+                    help="admission closes this long after the last arrival")
     ap.add_argument("--mem-budget-gb", type=int, default=16)
+    ap.add_argument("--limited-share", type=float, default=0.5,
+                    help="served pool again under this share of its device bytes (0 skips)")
     ap.add_argument("--track-steps", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 3:
