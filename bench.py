@@ -136,7 +136,7 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}",
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -217,7 +217,8 @@ def cpu_baseline(grid, opts, seconds=15.0):
         o.solve(tol=0.0, max_iter=1, warm_start=True)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"{n} warm iterations (iterations 2..{n + 1} of a cold solve) of the "
                       f"{grid.nbus}-bus grid, single-threaded C oracle"}
 
@@ -244,7 +245,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": workload_config(grid, opts, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                             "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} warm ADMM iterations of the {grid.nbus}-bus "
                                        "grid after a cold start and warm-up, single-threaded"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -596,12 +598,16 @@ def run_ours(args):
         fs.close()
 
     # the one-level variant (z = 0, Mhanna et al.) on the same grid, as a speed
-    # comparison: time to the same tolerance from a cold start
-    tt1 = None
+    # comparison: time to the same tolerance from a cold start; and the
+    # two-level method with the adaptive outer penalty (beta_rule 1)
+    tt1 = tta = None
     if args.time_to_tol and args.one_level:
         s1 = admm.Solver(grid, stream=stream, two_level=0, **opts)
         tt1 = solve_timed(s1, stream, 1e-3, args.tol_max_iter, False)
         s1.close()
+        sa = admm.Solver(grid, stream=stream, beta_rule=1, **opts)
+        tta = solve_timed(sa, stream, 1e-3, args.tol_max_iter, False)
+        sa.close()
 
     # smaller grids of the same kind (2k, 10k): time to 1e-3 and to the
     # violation target, and the 2k objective against the oracle's own solve
@@ -617,6 +623,11 @@ def run_ours(args):
                    "rho_pq": o2["rho_pq"], "rho_va": o2["rho_va"],
                    "time_to_tol": solve_timed(s2, stream, 1e-3, args.tol_max_iter, False)}
             s2.close()
+            # the adaptive outer penalty (beta_rule 1), same grid and penalties
+            s5 = admm.Solver(g2, stream=stream, beta_rule=1, **o2)
+            rec["time_to_tol_adaptive_beta"] = solve_timed(s5, stream, 1e-3, args.tol_max_iter,
+                                                           False)
+            s5.close()
             if args.feasible:
                 s3 = admm.Solver(g2, stream=stream, **dict(o2, rho_pq=args.feas_rho[0],
                                                           rho_va=args.feas_rho[1]))
@@ -625,6 +636,11 @@ def run_ours(args):
                 rec["time_to_max_viol"].update({"rho_pq": args.feas_rho[0],
                                                 "rho_va": args.feas_rho[1]})
                 s3.close()
+                s6 = admm.Solver(g2, stream=stream, beta_rule=1,
+                                 **dict(o2, rho_pq=args.feas_rho[0], rho_va=args.feas_rho[1]))
+                rec["time_to_max_viol_adaptive_beta"] = time_to_violation(
+                    s6, stream, args.feas_target, args.feas_max_iter, 100)
+                s6.close()
                 # the one-level variant (z = 0) at its own penalties
                 s4 = admm.Solver(g2, stream=stream, two_level=0,
                                  **dict(o2, rho_pq=args.feas_rho1[0], rho_va=args.feas_rho1[1]))
@@ -711,6 +727,8 @@ def run_ours(args):
             line["time_to_max_viol"] = feas
         if tt1 is not None:
             line["time_to_tol_one_level"] = tt1
+        if tta is not None:
+            line["time_to_tol_adaptive_beta"] = tta
         if sizes is not None:
             line["grids"] = sizes
         if track is not None:
@@ -732,7 +750,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nbus", type=int, default=70000)

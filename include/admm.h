@@ -104,6 +104,9 @@ typedef struct {
     int32_t graph_body_iters; /* iterations per body of the WHILE node, 1..16 (1); the
                                  loop still stops after exactly the iteration that
                                  converges or reaches max_iter                       */
+    int32_t beta_rule;     /* outer penalty growth at an outer update: 0 (default) times
+                              beta_factor when ||z|| > z_decay ||z_prev||; 1 (adaptive)
+                              times min(beta_factor, max(1, (||z|| / (z_decay ||z_prev||))^2)) */
 } admm_options;
 
 typedef struct {

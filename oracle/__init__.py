@@ -43,7 +43,7 @@ OPT_DOUBLES = ("rho_pq", "rho_va", "obj_scale", "line_limit_frac", "beta0", "bet
                "z_decay", "beta_max", "lambda_max", "tol_in0", "tol_in_decay", "al_rho0",
                "al_tol", "al_decay", "al_rho_factor", "al_rho_max", "tron_gtol", "tron_ftol",
                "tron_xtol")
-OPT_INTS = ("two_level", "max_outer", "max_inner", "al_max_iter", "tron_max_iter", "pad_")
+OPT_INTS = ("two_level", "max_outer", "max_inner", "al_max_iter", "tron_max_iter", "beta_rule")
 
 
 class OraOptions(C.Structure):
@@ -75,7 +75,7 @@ def default_options(**kw) -> dict:
              tol_in0=1e-2, tol_in_decay=0.5, al_rho0=0.0, al_tol=1e-8, al_decay=0.25,
              al_rho_factor=100.0, al_rho_max=1e12, tron_gtol=1e-10, tron_ftol=1e-12, tron_xtol=1e-13,
              two_level=1, max_outer=20, max_inner=1000, al_max_iter=20, tron_max_iter=200,
-             pad_=0)
+             beta_rule=0)
     for k, v in kw.items():
         if k not in o:
             raise KeyError(k)

@@ -926,14 +926,24 @@ static double eps_dual(const ora *p, double t) { return sqrt((double)p->m) * t +
 /* Algorithm 1, outer update (readings of this implementation):
  * lam <- Proj_[-lambda_max, lambda_max](lam + beta z); beta <- beta_factor beta
  * (capped) when ||z|| did not fall below z_decay times its value at the
- * previous outer update; the inner tolerance halves each outer update. */
+ * previous outer update; the inner tolerance halves each outer update.
+ * The adaptive variant (beta_rule 1, Section V's sensitivity to the penalties)
+ * grows beta by (||z|| / (z_decay ||z_prev||))^2, kept within [1, beta_factor]:
+ * no growth while ||z|| falls fast enough, the full factor when it stalls. */
 static void outer_update(ora *p, double tol)
 {
     for (int c = 0; c < p->m; ++c) {
         double v = p->lam[c] + p->beta * p->z[c];
         p->lam[c] = proj1(v, -p->o.lambda_max, p->o.lambda_max);
     }
-    if (p->zn > p->o.z_decay * p->zprev) {
+    if (p->o.beta_rule == 1) {
+        double r = p->zn / (p->o.z_decay * p->zprev);     /* 0 while zprev is infinite */
+        double f = r * r;
+        if (!(f > 1.0)) f = 1.0;
+        if (f > p->o.beta_factor) f = p->o.beta_factor;
+        double b = p->beta * f;
+        p->beta = b < p->o.beta_max ? b : p->o.beta_max;
+    } else if (p->zn > p->o.z_decay * p->zprev) {
         double b = p->beta * p->o.beta_factor;
         p->beta = b < p->o.beta_max ? b : p->o.beta_max;
     }

@@ -34,7 +34,7 @@ _OPT_D = ("rho_pq", "rho_va", "obj_scale", "line_limit_frac", "beta0", "beta_fac
           "beta_max", "lambda_max", "tol_in0", "tol_in_decay", "al_rho0", "al_tol", "al_decay",
           "al_rho_factor", "al_rho_max", "tron_gtol", "tron_ftol", "tron_xtol")
 _OPT_I = ("two_level", "max_outer", "max_inner", "al_max_iter", "tron_max_iter", "use_graph",
-          "branch_blocks", "graph_body_iters")
+          "branch_blocks", "graph_body_iters", "beta_rule")
 
 
 class admm_options(C.Structure):

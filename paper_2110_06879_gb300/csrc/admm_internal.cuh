@@ -65,7 +65,7 @@ struct DevOpts {
     double beta0, beta_factor, z_decay, beta_max, lambda_max, tol_in0, tol_in_decay;
     double al_rho0, al_tol, al_decay, al_rho_factor, al_rho_max;
     double tron_gtol, tron_ftol, tron_xtol;
-    int32_t two_level, max_outer, max_inner, al_max_iter, tron_max_iter, pad;
+    int32_t two_level, max_outer, max_inner, al_max_iter, tron_max_iter, beta_rule;
 };
 
 struct DevGrid {

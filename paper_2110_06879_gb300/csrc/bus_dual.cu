@@ -448,7 +448,15 @@ bus_dual_kernel(DevGrid G, DevOpts O)
                 // beta grows when ||z|| stalled
                 c->pending = 1;
                 c->beta_used = c->beta;
-                if (zn > O.z_decay * c->zprev) c->beta = fmin(c->beta * O.beta_factor, O.beta_max);
+                if (O.beta_rule == 1) {
+                    // adaptive: grow by the squared shortfall of the decrease
+                    // (no growth the first time, zprev being infinite)
+                    const double r = zn / (O.z_decay * c->zprev);
+                    const double f = fmin(O.beta_factor, fmax(1.0, r * r));
+                    c->beta = fmin(c->beta * f, O.beta_max);
+                } else if (zn > O.z_decay * c->zprev) {
+                    c->beta = fmin(c->beta * O.beta_factor, O.beta_max);
+                }
                 c->zprev = zn;
                 c->outer += 1;
                 c->inner = 0;

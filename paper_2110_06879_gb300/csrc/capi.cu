@@ -193,6 +193,7 @@ int validate(const admm_grid *g, const admm_options *o)
             set_err("graph_body_iters must be in 1..%d", kMaxBodyIters);
             return ADMM_ERR_INVALID_ARG;
         }
+        if (o->beta_rule < 0 || o->beta_rule > 1) { set_err("beta_rule must be 0 or 1"); return ADMM_ERR_INVALID_ARG; }
         if (o->max_outer < 1 || o->max_inner < 1 || o->tron_max_iter < 1 || o->al_max_iter < 1) {
             set_err("iteration caps must be >= 1");
             return ADMM_ERR_INVALID_ARG;
@@ -609,6 +610,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     O.tron_gtol = op.tron_gtol; O.tron_ftol = op.tron_ftol; O.tron_xtol = op.tron_xtol;
     O.two_level = op.two_level; O.max_outer = op.max_outer; O.max_inner = op.max_inner;
     O.al_max_iter = op.al_max_iter; O.tron_max_iter = op.tron_max_iter;
+    O.beta_rule = op.beta_rule;
     // uploads (host staging in the device layout)
     {
         std::vector<double> bus(6 * (size_t)nb), raw(6 * (size_t)nl), gc(3 * (size_t)ng + 1),

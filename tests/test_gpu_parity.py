@@ -59,10 +59,12 @@ def test_admittance_and_cold_start():
 @pytest.mark.parametrize("seed,kw,devices", [(0, TINY, False), (1, TINY, False),
                                              (2, dict(rho_pq=10.0, rho_va=1e3), False),
                                              (3, dict(TINY, two_level=0), False),
-                                             (1, TINY, True), (5, TINY, True)])
+                                             (1, TINY, True), (5, TINY, True),
+                                             (7, dict(TINY, beta_rule=1, max_inner=2), False)])
 def test_first_ten_iterations(seed, kw, devices):
     """Every iterate of the first ten iterations; devices: bus shunts,
-    transformers and phase shifters."""
+    transformers and phase shifters; beta_rule 1: the adaptive outer penalty,
+    with an outer update every second iteration."""
     grid = synth.tiny_grid(seed, devices=devices)
     s = admm.Solver(grid, **kw)
     for k in range(1, 11):
@@ -74,7 +76,7 @@ def test_first_ten_iterations(seed, kw, devices):
         r, ro = s.residuals(), o.residuals()
         assert r["iters"] == ro["iters"] == k
         assert r["outer_iters"] == ro["outer_iters"]
-        assert r["beta"] == ro["beta"]
+        assert r["beta"] == pytest.approx(ro["beta"], rel=1e-9)
 
 
 def test_converged_solve_matches_oracle():

@@ -594,3 +594,46 @@ def test_branch_al_loop_solves_line_limited_problem(oracle_mod, binding):
             assert abs(mu.get(e, 0.0) - lt[e]) <= 1e-5 * mscale, (it, mu, lt)
     if binding:
         assert n_active >= 10     # the limits do bind in these problems
+
+
+def test_adaptive_outer_penalty_rule(oracle_mod):
+    """The adaptive outer update (beta_rule 1) with max_inner = 1, one outer
+    update per iteration: lam <- Proj(lam + beta z) as before, and
+    beta_{k+1} = beta_k * min(6, max(1, (||z_k|| / (0.8 ||z_{k-1}||))^2)),
+    no growth at the first update; checked against the z norms of runs of
+    one to four iterations."""
+    grid = synth.tiny_grid(2)
+    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5, max_inner=1, beta_rule=1)
+    runs = []
+    for k in (1, 2, 3, 4):
+        o = oracle_mod.Oracle(grid, **kw)
+        o.solve(tol=0.0, max_iter=k)
+        runs.append(o)
+    zn = [np.linalg.norm(r.get(oracle_mod.Z)) for r in runs]
+    betas = [r.residuals()["beta"] for r in runs]
+    lam = [r.get(oracle_mod.LAMBDA) for r in runs]
+    z = [r.get(oracle_mod.Z) for r in runs]
+    assert betas[0] == 1e5
+    grew = False
+    for k in range(1, 4):
+        f = min(6.0, max(1.0, (zn[k] / (0.8 * zn[k - 1])) ** 2))
+        assert betas[k] == pytest.approx(betas[k - 1] * f, rel=1e-12)
+        grew = grew or f > 1.0
+        np.testing.assert_allclose(lam[k], lam[k - 1] + betas[k - 1] * z[k], rtol=1e-12, atol=1e-12)
+    assert grew     # the sequence exercises the growth, not only the floor
+
+
+def test_adaptive_outer_penalty_converges(oracle_mod):
+    """The whole method with the adaptive outer penalty still converges on the
+    30-bus grid to the same point as the fixed rule (cost within 1e-5, AC
+    violation below 1e-3); its gentler growth takes more outer updates (20
+    against 16 at tol 1e-6), so the outer cap is raised to 40 for both."""
+    grid = synth.tiny_grid(0)
+    kw = dict(rho_pq=1e3, rho_va=1e4, beta0=1e5, max_outer=40)
+    a = oracle_mod.Oracle(grid, **kw)
+    b = oracle_mod.Oracle(grid, beta_rule=1, **kw)
+    assert a.solve(tol=1e-6, max_iter=30000) == 0
+    assert b.solve(tol=1e-6, max_iter=30000) == 0
+    fa, fb = a.finalize(), b.finalize()
+    assert abs(fa["objective"] - fb["objective"]) <= 1e-5 * fa["objective"]
+    assert fb["max_viol"] <= 1e-3
