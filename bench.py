@@ -366,7 +366,7 @@ def run_batched(args, admm, stream, device=None):
     grids = [grids_all[k] for k in mine]
     kw = dict(rho_pq=3e3, rho_va=3e4)
     b = admm.Solver(grids, stream=stream, **kw)
-    blocks, body, _ = b.autotune(2)
+    blocks, body, _, lanes = b.autotune(2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     b.solve(tol=1e-3, max_iter=3000)        # cold start of every scenario
@@ -393,6 +393,7 @@ def run_batched(args, admm, stream, device=None):
             "ranks": ws, "sharding": "longest first by buses, no collective on the data path",
             "iters_p50": int(np.median(it)), "iters_max": int(it.max()),   # rank 0's scenarios
             "autotuned_branch_blocks": blocks, "autotuned_graph_body_iters": body,
+            "autotuned_lanes_per_branch": lanes,
             "plain_loop_sample": len(sample),
             "plain_loop_scenarios_per_s": len(sample) / tloop if tloop > 0 else None,
             "speedup_vs_plain_loop": (n_all / dt) / (len(sample) / tloop) if tloop > 0 else None,
@@ -490,6 +491,7 @@ def run_served(args, admm, stream):
             "pool_buses": int(sum(sizes)),
             "autotuned_branch_blocks": tuned[0] if tuned else None,
             "autotuned_graph_body_iters": tuned[1] if tuned else None,
+            "autotuned_lanes_per_branch": tuned[3] if tuned else None,
             "pool_cold_solve_s": max(p["warm"] for p in info),
             "rates": per_rate, "memory_limited": limited,
             "tol": 1e-3, "max_iter_per_request": 500, "tick_iters": 8}
@@ -649,6 +651,23 @@ def run_ours(args):
                 rec["time_to_max_viol_one_level"].update({"rho_pq": args.feas_rho1[0],
                                                           "rho_va": args.feas_rho1[1]})
                 s4.close()
+            if nb == args.lanes_nbus:
+                # one lane against two lanes per branch on the same iterations
+                # (iterations 6-25 of a cold solve), and the autotuner's pick
+                lc = {}
+                for lanes in (1, 2):
+                    sl = admm.Solver(g2, stream=stream, lanes_per_branch=lanes, **o2)
+                    sl.solve(tol=0.0, max_iter=5)
+                    pr = [sl.profile_iterations(1) for _ in range(20)]
+                    lc[f"lanes_{lanes}_branch_ms"] = sum(p["branch_ms"] for p in pr) / len(pr)
+                    sl.close()
+                st_ = admm.Solver(g2, stream=stream, **o2)
+                st_.solve(tol=0.0, max_iter=5)
+                tb, tbody, tms, tl = st_.autotune(2)
+                st_.close()
+                lc.update({"autotuned_lanes_per_branch": tl, "autotuned_branch_blocks": tb,
+                           "autotuned_branch_ms": tms})
+                rec["lanes_per_branch"] = lc
             gpu_iters = rec["time_to_tol"]["iters"]
             if rank == 0 and nb <= args.gap_max_nbus and gpu_iters > args.gap_max_iter:
                 rec["oracle"] = {"skipped": f"the GPU solve took {gpu_iters} iterations; the "
@@ -771,6 +790,8 @@ def main():
     ap.add_argument("--size-rho", type=float, nargs=2, default=[3e3, 3e4])
     ap.add_argument("--gap-max-nbus", type=int, default=2000,
                     help="largest grid whose objective is compared with an oracle solve")
+    ap.add_argument("--lanes-nbus", type=int, default=10000,
+                    help="grid of --sizes on which one and two lanes per branch are compared")
     ap.add_argument("--gap-max-iter", type=int, default=1500,
                     help="longest GPU solve (iterations) the oracle comparison repeats")
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")

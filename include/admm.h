@@ -107,6 +107,10 @@ typedef struct {
     int32_t beta_rule;     /* outer penalty growth at an outer update: 0 (default) times
                               beta_factor when ||z|| > z_decay ||z_prev||; 1 (adaptive)
                               times min(beta_factor, max(1, (||z|| / (z_decay ||z_prev||))^2)) */
+    int32_t lanes_per_branch; /* lanes solving one branch subproblem: 1 (0 means 1) or 2
+                                 (a lane pair splits the two line ends' flows and the
+                                 rows of the 6x6 products; the iterates agree with the
+                                 one-lane kernel to rounding, not bitwise)           */
 } admm_options;
 
 typedef struct {
@@ -309,23 +313,23 @@ int admm_dual_update_noalloc(int64_t m, const double *d_u, const double *d_xbar,
                              const double *d_lambda, double beta, int32_t two_level,
                              double *d_z, double *d_y, double *d_norms, void *cuda_stream);
 
-/* Autotuner over the launch shape, never over results.  (1) Resident
- * branch_tron blocks: 5 counts (1/2, 3/4, 1, 3/2 and 2 blocks of 128 lanes
- * per SM), each timed on the same `iters` warm iterations of every scenario
- * replayed from a device copy of the current state, twice (forward and reverse
- * order); the fastest mean branch_tron time wins.  (2) With the graph path,
- * iterations per body of the WHILE node (1, 2, 4), each timed through the
- * graph over 4 * iters replayed iterations.  The choice is kept for later
- * solves (the graph is rebuilt) and the state is put back, so the tuner
- * changes no result and no iteration count.  Lanes per branch are fixed at
- * one: a branch's TRON iteration is a chain of dependent 6x6 operations and
- * GB300's FP64 pipe costs the same per warp instruction at any lane count.
- * Allocates one temporary device buffer the size of the iteration state
- * (ADMM_ERR_OOM if that fails).  Outputs may be NULL: *blocks_out the block
- * count, *body_out the iterations per graph body, *ms_best the fastest mean
- * branch_tron time in ms. */
+/* Autotuner over the launch shape.  (1) Lanes per branch and resident
+ * branch_tron blocks: one lane with 1/2, 3/4, 1, 3/2 or 2 blocks of 128 lanes
+ * per SM, two lanes with 1 or 2 blocks per SM; each candidate is timed on the
+ * same `iters` warm iterations of every scenario replayed from a device copy
+ * of the current state, twice (forward and reverse order); the fastest mean
+ * branch_tron time wins.  (2) With the graph path, iterations per body of the
+ * WHILE node (1, 2, 4), each timed through the graph over 4 * iters replayed
+ * iterations.  The choice is kept for later solves (the graph is rebuilt) and
+ * the state is put back, so the tuner changes no iteration of the current
+ * state; the block count and the graph shape never change a result, the lane
+ * count changes iterates at rounding level.  Allocates one temporary device
+ * buffer the size of the iteration state (ADMM_ERR_OOM if that fails).
+ * Outputs may be NULL: *blocks_out the block count, *body_out the iterations
+ * per graph body, *ms_best the fastest mean branch_tron time in ms,
+ * *lanes_out the lanes per branch. */
 int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
-                  double *ms_best);
+                  double *ms_best, int32_t *lanes_out);
 
 /* Roofline calibration (the paper has no counterpart): one launch of an
  * FP64-FMA-only kernel (2 blocks of 256 threads per SM, eight independent FMA

@@ -34,7 +34,7 @@ _OPT_D = ("rho_pq", "rho_va", "obj_scale", "line_limit_frac", "beta0", "beta_fac
           "beta_max", "lambda_max", "tol_in0", "tol_in_decay", "al_rho0", "al_tol", "al_decay",
           "al_rho_factor", "al_rho_max", "tron_gtol", "tron_ftol", "tron_xtol")
 _OPT_I = ("two_level", "max_outer", "max_inner", "al_max_iter", "tron_max_iter", "use_graph",
-          "branch_blocks", "graph_body_iters", "beta_rule")
+          "branch_blocks", "graph_body_iters", "beta_rule", "lanes_per_branch")
 
 
 class admm_options(C.Structure):
@@ -90,7 +90,7 @@ def lib():
             "admm_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_size_t)]),
             "admm_set_state": (C.c_int, [vp, vp, C.c_size_t]),
             "admm_profile_iterations": (C.c_int, [vp, i32, vp]),
-            "admm_autotune": (C.c_int, [vp, i32, vp, vp, vp]),
+            "admm_autotune": (C.c_int, [vp, i32, vp, vp, vp, vp]),
             "admm_dual_update_noalloc": (C.c_int, [C.c_int64, vp, vp, vp, vp, vp, d, i32, vp, vp,
                                                    vp, vp]),
             "admm_fp64_peak": (C.c_int, [i32, vp, vp]),
@@ -320,13 +320,14 @@ class Solver:
 
     def autotune(self, iters=3):
         """Tune the launch shape; returns (branch blocks, iterations per graph
-        body, fastest mean branch_tron ms)."""
+        body, fastest mean branch_tron ms, lanes per branch)."""
         n = C.c_int32(0)
         body = C.c_int32(0)
         ms = C.c_double(0.0)
-        _check(lib().admm_autotune(self.h, iters, C.byref(n), C.byref(body), C.byref(ms)),
-               "admm_autotune")
-        return int(n.value), int(body.value), float(ms.value)
+        lanes = C.c_int32(0)
+        _check(lib().admm_autotune(self.h, iters, C.byref(n), C.byref(body), C.byref(ms),
+                                   C.byref(lanes)), "admm_autotune")
+        return int(n.value), int(body.value), float(ms.value), int(lanes.value)
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)

@@ -119,6 +119,7 @@ __global__ void cold_start_kernel(DevGrid G, Range R, double beta_init);
 __global__ void slot_begin_kernel(DevGrid G, DevOpts O, int32_t s0, int32_t s1, SolveParams P);
 __global__ void run_begin_kernel(DevGrid G, int32_t run_max);
 __global__ void branch_tron_kernel(DevGrid G, DevOpts O);
+__global__ void branch_tron2_kernel(DevGrid G, DevOpts O);   // two lanes per branch
 __global__ void bus_dual_kernel(DevGrid G, DevOpts O);
 __global__ void control_kernel(DevGrid G, cudaGraphConditionalHandle cond, int32_t use_cond);
 __global__ void flush_lambda_kernel(DevGrid G, DevOpts O);

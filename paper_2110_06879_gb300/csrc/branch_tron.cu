@@ -80,6 +80,18 @@ __device__ __forceinline__ double amax(double m, double a)
     return ba > __double_as_longlong(m) ? __longlong_as_double(ba) : m;
 }
 
+// Two lanes per branch (kL = 2): lanes 2k and 2k+1 hold the same branch and
+// the same state, bit for bit; the parts of a trip that split cleanly (the two
+// line ends' flows, rows of 6x6 products, halves of 6-vector dot products)
+// are computed half on each lane and exchanged.  Every combined value is a
+// single sum mine + partner's, which is the same on both lanes (IEEE addition
+// commutes), so both lanes keep taking the same decisions.  m is the mask of
+// the lanes executing the call; pairs are always both in or both out, and
+// every lane named in m must reach the call: never place one of these products
+// behind a short-circuit (&&, ||, ?:) that some lanes of m skip.
+__device__ __forceinline__ bool odd_lane() { return (threadIdx.x & 1) != 0; }
+__device__ __forceinline__ double partner(unsigned m, double v) { return __shfl_xor_sync(m, v, 1); }
+
 // bounds of one branch: v_i, v_j from the buses, theta copies +-2 pi, slacks;
 // kept with their keys
 struct Bounds {
@@ -141,11 +153,32 @@ __device__ __forceinline__ void flow(double a, double al, double be, double vi, 
     o.h22 = -vv * T;
 }
 
+// One flow of either end (od: the to end, whose self term is in v_j), as
+// flow<true> / flow<false> with the choice made by selection, not a branch.
+__device__ __forceinline__ void flow_end(bool od, double a, double al, double be, double vi,
+                                         double vj, double vv, double c, double s, Flow &o)
+{
+    const double T = al * c + be * s;
+    const double Tp = be * c - al * s;
+    const double vk = od ? vj : vi;
+    const double ds = 2.0 * a * vk;
+    o.F = a * vk * vk + vv * T;
+    o.d0 = (od ? 0.0 : ds) + vj * T;
+    o.d1 = (od ? ds : 0.0) + vi * T;
+    o.d2 = vv * Tp;
+    o.h00 = od ? 0.0 : 2.0 * a;
+    o.h11 = od ? 2.0 * a : 0.0;
+    o.h01 = T;
+    o.h02 = vj * Tp;
+    o.h12 = vi * Tp;
+    o.h22 = -vv * T;
+}
+
 // f, gradient, packed Hessian and the four flows of eq. branch at x.
 // Y and t live in shared memory with stride kBranchBlock.
-__device__ __forceinline__ void evaluate(const double *sY, const double *sT, double rpq, double rva,
-                                         double lt0, double lt1, double rt, const double *x,
-                                         double &f, double *g, SMat H, double *F)
+__device__ __forceinline__ void evaluate1(const double *sY, const double *sT, double rpq, double rva,
+                                          double lt0, double lt1, double rt, const double *x,
+                                          double &f, double *g, SMat H, double *F)
 {
     const double vi = x[0], vj = x[1];
     double s, c;
@@ -228,37 +261,181 @@ __device__ __forceinline__ void evaluate(const double *sY, const double *sT, dou
     H[P(5, 5)] = rt;
 }
 
-__device__ __forceinline__ double dot6(const double *a, const double *b)
+// The same with two lanes per branch: the even lane takes the from end's two
+// flows (p_ij, q_ij), the odd lane the to end's (p_ji, q_ji); each forms its
+// end's shares of the gradient and Hessian sums, the pair swaps them and both
+// assemble f, g and H from (from-end share + to-end share).
+__device__ __forceinline__ void evaluate2(unsigned m, const double *sY, const double *sT,
+                                          double rpq, double rva, double lt0, double lt1,
+                                          double rt, const double *x, double &f, double *g,
+                                          SMat H, double *F)
+{
+    const bool od = odd_lane();
+    const double vi = x[0], vj = x[1];
+    double s, c;
+    sincos(x[2] - x[3], &s, &c);
+    const double vv = vi * vj;
+    constexpr int S = kBranchBlock;
+    const double gii = sY[0 * S], bii = sY[1 * S], gij = sY[2 * S], bij = sY[3 * S];
+    const double gji = sY[4 * S], bji = sY[5 * S], gjj = sY[6 * S], bjj = sY[7 * S];
+    Flow fl[2];
+    flow_end(od, od ? gjj : gii, od ? gji : gij, od ? -bji : bij, vi, vj, vv, c, s, fl[0]);
+    flow_end(od, od ? -bjj : -bii, od ? -bji : -bij, od ? -gji : gij, vi, vj, vv, c, s, fl[1]);
+    const double hm = fl[0].F * fl[0].F + fl[1].F * fl[1].F + (od ? x[5] : x[4]);
+    const double mum = (od ? lt1 : lt0) + rt * hm;
+    double G0 = 0.0, G1 = 0.0, G2 = 0.0, fq = 0.0;
+    double A00 = 0.0, A11 = 0.0, A01 = 0.0, A02 = 0.0, A12 = 0.0, A22 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double r = fl[k].F - sT[(od ? 2 + k : k) * S];
+        fq += r * r;
+        const double ck = rpq * r + 2.0 * mum * fl[k].F;
+        const double wk = rpq + 2.0 * mum;
+        G0 += ck * fl[k].d0;
+        G1 += ck * fl[k].d1;
+        G2 += ck * fl[k].d2;
+        A00 += ck * fl[k].h00 + wk * fl[k].d0 * fl[k].d0;
+        A11 += ck * fl[k].h11 + wk * fl[k].d1 * fl[k].d1;
+        A01 += ck * fl[k].h01 + wk * fl[k].d0 * fl[k].d1;
+        A02 += ck * fl[k].h02 + wk * fl[k].d0 * fl[k].d2;
+        A12 += ck * fl[k].h12 + wk * fl[k].d1 * fl[k].d2;
+        A22 += ck * fl[k].h22 + wk * fl[k].d2 * fl[k].d2;
+    }
+    // gradient of my end's h in (v_i, v_j, th)
+    const double em0 = 2.0 * (fl[0].F * fl[0].d0 + fl[1].F * fl[1].d0);
+    const double em1 = 2.0 * (fl[0].F * fl[0].d1 + fl[1].F * fl[1].d1);
+    const double em2 = 2.0 * (fl[0].F * fl[0].d2 + fl[1].F * fl[1].d2);
+    // swap with the partner; (from, to) in a fixed order on both lanes
+    const double pG0 = partner(m, G0), pG1 = partner(m, G1), pG2 = partner(m, G2);
+    const double pA00 = partner(m, A00), pA11 = partner(m, A11), pA01 = partner(m, A01);
+    const double pA02 = partner(m, A02), pA12 = partner(m, A12), pA22 = partner(m, A22);
+    const double pfq = partner(m, fq), ph = partner(m, hm);
+    const double pe0 = partner(m, em0), pe1 = partner(m, em1), pe2 = partner(m, em2);
+    const double pF0 = partner(m, fl[0].F), pF1 = partner(m, fl[1].F);
+    G0 += pG0; G1 += pG1; G2 += pG2;
+    A00 += pA00; A11 += pA11; A01 += pA01; A02 += pA02; A12 += pA12; A22 += pA22;
+    fq += pfq;
+    const double h0 = od ? ph : hm, h1 = od ? hm : ph;
+    const double mu0 = lt0 + rt * h0, mu1 = lt1 + rt * h1;
+    const double e00 = od ? pe0 : em0, e01 = od ? pe1 : em1, e02 = od ? pe2 : em2;
+    const double e10 = od ? em0 : pe0, e11 = od ? em1 : pe1, e12 = od ? em2 : pe2;
+    F[0] = od ? pF0 : fl[0].F;
+    F[1] = od ? pF1 : fl[1].F;
+    F[2] = od ? fl[0].F : pF0;
+    F[3] = od ? fl[1].F : pF1;
+    A00 += rt * (e00 * e00 + e10 * e10);
+    A11 += rt * (e01 * e01 + e11 * e11);
+    A01 += rt * (e00 * e01 + e10 * e11);
+    A02 += rt * (e00 * e02 + e10 * e12);
+    A12 += rt * (e01 * e02 + e11 * e12);
+    A22 += rt * (e02 * e02 + e12 * e12);
+    const double rwi = vi * vi - sT[4 * S], rti = x[2] - sT[5 * S];
+    const double rwj = vj * vj - sT[6 * S], rtj = x[3] - sT[7 * S];
+    f = 0.5 * rpq * fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
+      + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
+    g[0] = G0 + 2.0 * rva * rwi * vi;
+    g[1] = G1 + 2.0 * rva * rwj * vj;
+    g[2] = G2 + rva * rti;
+    g[3] = -G2 + rva * rtj;
+    g[4] = mu0;
+    g[5] = mu1;
+    H[P(0, 0)] = A00 + rva * (4.0 * vi * vi + 2.0 * rwi);
+    H[P(0, 1)] = A01;
+    H[P(0, 2)] = A02;
+    H[P(0, 3)] = -A02;
+    H[P(0, 4)] = rt * e00;
+    H[P(0, 5)] = rt * e10;
+    H[P(1, 1)] = A11 + rva * (4.0 * vj * vj + 2.0 * rwj);
+    H[P(1, 2)] = A12;
+    H[P(1, 3)] = -A12;
+    H[P(1, 4)] = rt * e01;
+    H[P(1, 5)] = rt * e11;
+    H[P(2, 2)] = A22 + rva;
+    H[P(2, 3)] = -A22;
+    H[P(2, 4)] = rt * e02;
+    H[P(2, 5)] = rt * e12;
+    H[P(3, 3)] = A22 + rva;
+    H[P(3, 4)] = -rt * e02;
+    H[P(3, 5)] = -rt * e12;
+    H[P(4, 4)] = rt;
+    H[P(4, 5)] = 0.0;
+    H[P(5, 5)] = rt;
+}
+
+template <int kL>
+__device__ __forceinline__ void evaluate(unsigned m, const double *sY, const double *sT, double rpq,
+                                         double rva, double lt0, double lt1, double rt,
+                                         const double *x, double &f, double *g, SMat H, double *F)
+{
+    if constexpr (kL == 1) evaluate1(sY, sT, rpq, rva, lt0, lt1, rt, x, f, g, H, F);
+    else evaluate2(m, sY, sT, rpq, rva, lt0, lt1, rt, x, f, g, H, F);
+}
+
+template <int kL = 1>
+__device__ __forceinline__ double dot6(const double *a, const double *b, unsigned m = kFull)
 {
     double s = 0.0;
+    if constexpr (kL == 1) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) s += a[i] * b[i];
-    return s;
-}
-
-__device__ __forceinline__ void hmul(SMat H, const double *v, double *o)
-{
+        for (int i = 0; i < 6; ++i) s += a[i] * b[i];
+        return s;
+    } else {
+        const bool od = odd_lane();   // even lane: entries 0..2, odd lane: 3..5
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) s += H[P(i, j)] * v[j];
-        o[i] = s;
+        for (int i = 0; i < 3; ++i) s += (od ? a[3 + i] : a[i]) * (od ? b[3 + i] : b[i]);
+        return s + partner(m, s);
     }
 }
 
-// q(s) = g's + s'Hs/2 using the symmetry of H
-__device__ __forceinline__ double qmodel(const double *g, SMat H, const double *s)
+template <int kL = 1>
+__device__ __forceinline__ void hmul(SMat H, const double *v, double *o, unsigned m = kFull)
 {
-    double q = 0.0;
+    if constexpr (kL == 1) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double t = g[i] + 0.5 * H[P(i, i)] * s[i];
+        for (int i = 0; i < 6; ++i) {
+            double s = 0.0;
 #pragma unroll
-        for (int j = i + 1; j < 6; ++j) t += H[P(i, j)] * s[j];
-        q += s[i] * t;
+            for (int j = 0; j < 6; ++j) s += H[P(i, j)] * v[j];
+            o[i] = s;
+        }
+    } else {
+        const bool od = odd_lane();   // even lane: rows 0..2, odd lane: rows 3..5
+        double r[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) s += H[od ? P(3 + i, j) : P(i, j)] * v[j];
+            r[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double q = partner(m, r[i]);
+            o[i] = od ? q : r[i];
+            o[3 + i] = od ? r[i] : q;
+        }
     }
-    return q;
+}
+
+// q(s) = g's + s'Hs/2 using the symmetry of H (two lanes: from H s by rows)
+template <int kL = 1>
+__device__ __forceinline__ double qmodel(const double *g, SMat H, const double *s, unsigned m = kFull)
+{
+    if constexpr (kL == 1) {
+        double q = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double t = g[i] + 0.5 * H[P(i, i)] * s[i];
+#pragma unroll
+            for (int j = i + 1; j < 6; ++j) t += H[P(i, j)] * s[j];
+            q += s[i] * t;
+        }
+        return q;
+    } else {
+        double hs[6];
+        hmul<2>(H, s, hs, m);
+        return dot6<2>(g, s, m) + 0.5 * dot6<2>(s, hs, m);
+    }
 }
 
 __device__ __forceinline__ void pstep(const Bounds &B, const double *x, const double *g, double a,
@@ -293,6 +470,7 @@ __device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const
 // a bound), so |s|^2, g's and q(s) follow from |g_P|^2 and g_P' H g_P computed
 // once; trials past a breakpoint evaluate the projection in full.  qsc
 // returns q(s) of the step chosen, from the same closed form or evaluation.
+template <int kL>
 __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x, const double *g,
                                        SMat H, double d2, double &alpha, double *s,
                                        double &qsc, Cnt &c)
@@ -307,8 +485,8 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         gp[i] = path[i] ? g[i] : 0.0;
     }
     double hg[6];
-    hmul(H, gp, hg);
-    const double G2 = dot6(gp, gp), GHG = dot6(gp, hg);
+    hmul<kL>(H, gp, hg);
+    const double G2 = dot6<kL>(gp, gp), GHG = dot6<kL>(gp, hg);
     // sufficient decrease and radius test at alpha = a (uniform across the
     // warp), with q(s(a)) in q
     auto ok_at = [&](double a, bool need, double &q) -> bool {
@@ -321,8 +499,11 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         if (__any_sync(kFull, need && !unc)) {
             double t[6];
             pstep(B, x, g, a, t);
-            const double qf = qmodel(g, H, t);
-            const bool okf = dle(dot6(t, t), d2) && dle(qf, kMu0 * dot6(g, t));
+            // every lane forms every product (no short-circuit): with two
+            // lanes per branch the products exchange values within the pair
+            const double qf = qmodel<kL>(g, H, t);
+            const double tt = dot6<kL>(t, t), gt = dot6<kL>(g, t);
+            const bool okf = dle(tt, d2) && dle(qf, kMu0 * gt);
             ok = unc ? ok : okf;
             q = unc ? q : qf;
         }
@@ -356,9 +537,10 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
     if (on) alpha = a;
 }
 
+template <int kL>
 __device__ __forceinline__ double boundary_tau(const double *a, const double *pv, double d2)
 {
-    const double pp = dot6(pv, pv), ap = dot6(a, pv), aa = dot6(a, a);
+    const double pp = dot6<kL>(pv, pv), ap = dot6<kL>(a, pv), aa = dot6<kL>(a, a);
     const double rad = dmaxi(d2 - aa, 0.0);
     const double disc = sqrt(ap * ap + pp * rad);
     if (!dpos(pp)) return 0.0;
@@ -455,6 +637,7 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
 // a projected backtracking search along the CG direction.
+template <int kL>
 __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
                                          SMat H, double d2, const double *sc, double qc,
                                          double *s, double &qs, Cnt &c)
@@ -474,7 +657,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     const bool act = on && any;
     if (!__any_sync(kFull, act)) return;
     double gc[6];
-    hmul(H, sc, gc);
+    hmul<kL>(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
     double L[21], dinv[6];
@@ -504,7 +687,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     for (int it = 0; it < kCgMaxit; ++it) {
         if (!__any_sync(kFull, go)) break;
         if (go) c.cg++;
-        hmul(H, pv, q);
+        hmul<kL>(H, pv, q);
         double kappa = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -524,7 +707,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         // negative curvature or the trust-region boundary: stop on the boundary
         const bool bnd = go && (!dpos(kappa) || dle(d2, nx2));
         if (__any_sync(kFull, bnd)) {
-            const double tau = boundary_tau(cur, pv, d2);
+            const double tau = boundary_tau<kL>(cur, pv, d2);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 w[i] = bnd ? w[i] + tau * pv[i] : w[i];
@@ -586,8 +769,9 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
                 double dd[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) dd[i] = sb[i] - sc[i];
-                const double qf = qmodel(g, H, sb);
-                const bool okf = ps && dle(qf, qc + kMu0 * dot6(gc, dd));
+                const double qf = qmodel<kL>(g, H, sb);
+                const double gdd = dot6<kL>(gc, dd);          // on every lane (see cauchy)
+                const bool okf = ps && dle(qf, qc + kMu0 * gdd);
                 qb = unc ? qb : qf;
                 okp = unc ? okp : okf;
             }
@@ -639,8 +823,9 @@ enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE =
 
 }  // namespace
 
-__global__ void __launch_bounds__(kBranchBlock, kBranchBlocksPerSM)
-branch_tron_kernel(DevGrid G, DevOpts O)
+// The kernel body, for kL = 1 or 2 lanes per branch.
+template <int kL>
+__device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
 {
     __shared__ double sh[16 * kBranchBlock];   // per lane: Y[8], t[8], stride kBranchBlock
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
@@ -664,9 +849,13 @@ branch_tron_kernel(DevGrid G, DevOpts O)
     }
     __syncthreads();
     const bool ordered = cstart[kClasses] == (unsigned)nl;
-    // the first `lanes` positions of the queue are dealt across all warps
-    const unsigned lanes = gridDim.x * blockDim.x;
-    const unsigned nwarps = lanes >> 5;
+    // branch slots: one per lane, or one per lane pair (the even lane, `lead`,
+    // takes part in the queue, files, writes and counts); the first `slots`
+    // positions of the queue are dealt across all warps
+    const bool lead = kL == 1 || !odd_lane();
+    const unsigned slots = gridDim.x * blockDim.x / kL;
+    const unsigned spw = 32 / kL;                    // slots per warp
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     const int32_t *lcur = G.cls_list + (size_t)cur * kClasses * nl;
     int32_t *lnxt = G.cls_list + (size_t)nxt * kClasses * nl;
 
@@ -697,8 +886,9 @@ branch_tron_kernel(DevGrid G, DevOpts O)
         if (__any_sync(kFull, go_t)) {
             double sc[6], s[6];
             double qs = 0.0, qsc = 0.0;
-            cauchy(go_t, B, x, g, H, dsq, alpha, sc, qsc, c);
-            subspace(go_t, B, x, g, H, dsq, sc, qsc, s, qs, c);
+            cauchy<kL>(go_t, B, x, g, H, dsq, alpha, sc, qsc, c);
+            subspace<kL>(go_t, B, x, g, H, dsq, sc, qsc, s, qs, c);
+            const double s2 = dot6<kL>(s, s);
             if (go_t) {
                 double xn = 0.0, sn = 0.0;
 #pragma unroll
@@ -716,7 +906,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                     } else {
 #pragma unroll
                         for (int i = 0; i < 6; ++i) xt[i] = B.clamp(i, x[i] + s[i]);
-                        snorm2 = dot6(s, s);
+                        snorm2 = s2;
                         eval = true;
                     }
                 }
@@ -738,18 +928,20 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 fin = apass >= O.al_max_iter;
             }
             if (fin) {
+                if (lead) {
 #pragma unroll
-                for (int i = 0; i < 6; ++i) G.bx[i * nl + b] = x[i];
-                G.blt[b] = lt0;
-                G.blt[nl + b] = lt1;
-                G.balpha[b] = alpha;
+                    for (int i = 0; i < 6; ++i) G.bx[i * nl + b] = x[i];
+                    G.blt[b] = lt0;
+                    G.blt[nl + b] = lt1;
+                    G.balpha[b] = alpha;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) G.bu[i * nl + b] = F[i];
-                G.bu[4 * nl + b] = x[0] * x[0];
-                G.bu[5 * nl + b] = x[2];
-                G.bu[6 * nl + b] = x[1] * x[1];
-                G.bu[7 * nl + b] = x[3];
-                filed = b;
+                    for (int i = 0; i < 4; ++i) G.bu[i * nl + b] = F[i];
+                    G.bu[4 * nl + b] = x[0] * x[0];
+                    G.bu[5 * nl + b] = x[2];
+                    G.bu[6 * nl + b] = x[1] * x[1];
+                    G.bu[7 * nl + b] = x[3];
+                    filed = b;
+                }
                 fcls = trip_class(trips);
                 b = -1;
                 state = LS_IDLE;
@@ -762,15 +954,16 @@ branch_tron_kernel(DevGrid G, DevOpts O)
         // (R) refill idle lanes from the branch queue (one atomic per warp);
         // branches of scenarios that are not iterating are filed and skipped
         for (int rep = 0; rep < 64; ++rep) {
-            const unsigned need = __ballot_sync(kFull, state == LS_IDLE && !exhausted);
+            const unsigned need = __ballot_sync(kFull, lead && state == LS_IDLE && !exhausted);
             if (!need) break;
             const int leader = __ffs(need) - 1;
             unsigned base = 0;
             if (lane == leader) base = atomicAdd(&ctrl->branch_next, (unsigned)__popc(need));
             base = __shfl_sync(kFull, base, leader);
+            unsigned idx = base + __popc(need & ((1u << lane) - 1u));
+            if constexpr (kL == 2) idx = __shfl_sync(kFull, idx, lane & ~1);   // the pair's slot
             int skip = -1;
             if (state == LS_IDLE && !exhausted) {
-                const unsigned idx = base + __popc(need & ((1u << lane) - 1u));
                 // the first fill hands each warp 32 consecutive positions:
                 // deal the ranks across the warps instead (rank = lane-in-fill
                 // x warps + warp), so that the hardest branches spread over all
@@ -779,7 +972,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                 // whose rank is past the end hold no branch; every position
                 // below `lanes` is still drawn, since each lane draws at least
                 // once and draws take consecutive positions.
-                const unsigned r = idx < lanes ? (idx & 31u) * nwarps + (idx >> 5) : idx;
+                const unsigned r = idx < slots ? (idx % spw) * nwarps + idx / spw : idx;
                 if (r < (unsigned)nl) {
                     int bb = (int)r;
                     if (ordered) {
@@ -830,7 +1023,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
                     exhausted = true;
                 }
             }
-            file_branches(ctrl, lnxt, nl, nxt, lane, skip, kClasses - 1);
+            file_branches(ctrl, lnxt, nl, nxt, lane, lead ? skip : -1, kClasses - 1);
         }
         // done when every lane is idle and the queue is drained
         if (!__any_sync(kFull, state != LS_IDLE || !exhausted)) break;
@@ -852,9 +1045,11 @@ branch_tron_kernel(DevGrid G, DevOpts O)
         }
         // (E) the one evaluation site of the trip
         double fe = 0.0;
-        if (eval) evaluate(sY, sT, rpq, rva, lt0, lt1, rt, xt, fe, g, H, F);
+        const unsigned em = __ballot_sync(kFull, eval);
+        if (eval) evaluate<kL>(em, sY, sT, rpq, rva, lt0, lt1, rt, xt, fe, g, H, F);
         if (b >= 0) ++trips;
         // (Q) after the evaluation
+        const unsigned im = __ballot_sync(kFull, state == LS_INIT);
         if (state == LS_INIT) {
             f = fe;
             c.tron_calls++;
@@ -862,7 +1057,7 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             gtol = O.tron_gtol * dmaxi(pgnorm(B, x, g), 1.0);
             double sp[6];
             pstep(B, x, g, 1.0, sp);
-            dsq = dot6(sp, sp);
+            dsq = dot6<kL>(sp, sp, im);
             alpha = dpos(alpha) ? alpha : 1.0;   // carried from the previous call
             k = 0;
             state = LS_ITER;
@@ -903,16 +1098,31 @@ branch_tron_kernel(DevGrid G, DevOpts O)
             ++k;
         }
     }
+    // counters: once per branch (the lead lane of a pair)
     unsigned long long *st = ctrl->stats;
-    warp_add_u64(&st[ST_TRON_CALLS], c.tron_calls);
-    warp_add_u64(&st[ST_TRON_ITERS], c.tron_iters);
-    warp_add_u64(&st[ST_FGH], c.fgh);
-    warp_add_u64(&st[ST_F], c.f);
-    warp_add_u64(&st[ST_CAUCHY], c.cauchy);
-    warp_add_u64(&st[ST_CG], c.cg);
-    warp_add_u64(&st[ST_PS], c.ps);
-    warp_add_u64(&st[ST_AL], c.al);
-    warp_add_u64(&st[ST_TRON_MAXHIT], c.maxhit);
+    const int on = lead ? 1 : 0;
+    warp_add_u64(&st[ST_TRON_CALLS], on * c.tron_calls);
+    warp_add_u64(&st[ST_TRON_ITERS], on * c.tron_iters);
+    warp_add_u64(&st[ST_FGH], on * c.fgh);
+    warp_add_u64(&st[ST_F], on * c.f);
+    warp_add_u64(&st[ST_CAUCHY], on * c.cauchy);
+    warp_add_u64(&st[ST_CG], on * c.cg);
+    warp_add_u64(&st[ST_PS], on * c.ps);
+    warp_add_u64(&st[ST_AL], on * c.al);
+    warp_add_u64(&st[ST_TRON_MAXHIT], on * c.maxhit);
+}
+
+__global__ void __launch_bounds__(kBranchBlock, kBranchBlocksPerSM)
+branch_tron_kernel(DevGrid G, DevOpts O)
+{
+    branch_tron_body<1>(G, O);
+}
+
+// two lanes per branch (a lane pair shares each branch's work, see evaluate2)
+__global__ void __launch_bounds__(kBranchBlock, kBranchBlocksPerSM)
+branch_tron2_kernel(DevGrid G, DevOpts O)
+{
+    branch_tron_body<2>(G, O);
 }
 
 }  // namespace admm

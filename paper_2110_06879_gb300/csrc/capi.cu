@@ -74,6 +74,7 @@ struct admm_handle {
     std::vector<double> base_mva;
     int32_t sel = 0;             // scenario addressed by the per-scenario calls
     int nblk_branch = 0, nblk_bus = 0, nblk_fin = 0, nblk_flush = 0;
+    int lanes = 1;               // lanes per branch of branch_tron (1 or 2)
     // iteration graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -194,6 +195,10 @@ int validate(const admm_grid *g, const admm_options *o)
             return ADMM_ERR_INVALID_ARG;
         }
         if (o->beta_rule < 0 || o->beta_rule > 1) { set_err("beta_rule must be 0 or 1"); return ADMM_ERR_INVALID_ARG; }
+        if (o->lanes_per_branch < 0 || o->lanes_per_branch > 2) {
+            set_err("lanes_per_branch must be 0, 1 or 2");
+            return ADMM_ERR_INVALID_ARG;
+        }
         if (o->max_outer < 1 || o->max_inner < 1 || o->tron_max_iter < 1 || o->al_max_iter < 1) {
             set_err("iteration caps must be >= 1");
             return ADMM_ERR_INVALID_ARG;
@@ -302,6 +307,25 @@ Layout layout_of(const Sizes &z)
     return L;
 }
 
+// branch_tron with one or two lanes per branch
+void *branch_func(int lanes)
+{
+    return lanes == 2 ? (void *)branch_tron2_kernel : (void *)branch_tron_kernel;
+}
+
+void launch_branch(int lanes, int nbk, cudaStream_t s, const DevGrid &G, const DevOpts &O)
+{
+    if (lanes == 2) branch_tron2_kernel<<<nbk, kBranchBlock, 0, s>>>(G, O);
+    else branch_tron_kernel<<<nbk, kBranchBlock, 0, s>>>(G, O);
+}
+
+// blocks that give every branch a slot (128 / lanes slots per block)
+int branch_blocks_needed(int nl, int lanes)
+{
+    const int per = kBranchBlock / lanes;
+    return (nl + per - 1) / per;
+}
+
 int launch_check(const char *what)
 {
     cudaError_t e = cudaGetLastError();
@@ -349,7 +373,7 @@ int build_graph(admm_handle *h)
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     void *bargs[2] = {&h->G, &h->O};
     cudaKernelNodeParams bp{};
-    bp.func = (void *)branch_tron_kernel;
+    bp.func = branch_func(h->lanes);
     bp.gridDim = dim3(h->nblk_branch);
     bp.blockDim = dim3(kBranchBlock);
     bp.kernelParams = bargs;
@@ -440,7 +464,7 @@ int run_async(admm_handle *h, int32_t run_max)
     if ((rc = launch_check("run_begin_kernel")) != ADMM_OK) return rc;
     cudaGraphConditionalHandle none = 0;
     for (int it = 0; it < run_max; ++it) {
-        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
+        launch_branch(h->lanes, h->nblk_branch, h->stream, h->G, h->O);
         bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
         control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
         if ((rc = launch_check("iteration kernels")) != ADMM_OK) return rc;
@@ -546,7 +570,8 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 152;
         cudaGetLastError();
-        const int need = (nl + kBranchBlock - 1) / kBranchBlock;
+        h->lanes = op.lanes_per_branch == 2 ? 2 : 1;
+        const int need = branch_blocks_needed(nl, h->lanes);
         const int cap = op.branch_blocks > 0 ? op.branch_blocks : sms * kBranchBlocksPerSM;
         h->nblk_branch = need < cap ? need : cap;
     }
@@ -1275,7 +1300,7 @@ int replay_copy(admm_handle *h, char *snap, bool save)
 }  // namespace
 
 extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out, int32_t *body_out,
-                             double *ms_best)
+                             double *ms_best, int32_t *lanes_out)
 {
     NvtxRange nvtx_("admm_autotune");
     if (!h || iters < 1) { set_err("bad argument"); return ADMM_ERR_INVALID_ARG; }
@@ -1284,10 +1309,15 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         sms = 152;
     cudaGetLastError();
-    const int need = (h->nl + kBranchBlock - 1) / kBranchBlock;
-    constexpr int kCand = 5;
-    const int cand[kCand] = {sms / 2, (3 * sms) / 4, sms, (3 * sms) / 2, 2 * sms};
-    double tot[kCand] = {0, 0, 0, 0, 0};
+    // (lanes per branch, blocks) candidates
+    constexpr int kCand = 7;
+    const int cand[kCand] = {sms / 2, (3 * sms) / 4, sms, (3 * sms) / 2, 2 * sms, sms, 2 * sms};
+    const int clan[kCand] = {1, 1, 1, 1, 1, 2, 2};
+    double tot[kCand] = {0, 0, 0, 0, 0, 0, 0};
+    auto blocks_of = [&](int c) {
+        const int need = branch_blocks_needed(h->nl, clan[c]);
+        return cand[c] < need ? (cand[c] > 0 ? cand[c] : 1) : need;
+    };
     size_t bytes = 0;
     for (auto &p : replay_parts(h)) bytes += (p.second + 255) & ~(size_t)255;
     char *snap = nullptr;
@@ -1304,7 +1334,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
     for (int pass = 0; pass < 2 && rc == ADMM_OK; ++pass) {
         for (int k = 0; k < kCand && rc == ADMM_OK; ++k) {
             const int c = pass == 0 ? k : kCand - 1 - k;
-            const int nbk = cand[c] < need ? (cand[c] > 0 ? cand[c] : 1) : need;
+            const int nbk = blocks_of(c);
             DevGrid G = h->G;
             G.nblk_branch = nbk;
             if ((rc = replay_copy(h, snap, false)) != ADMM_OK) break;
@@ -1313,7 +1343,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
             for (int it = 0; it < iters && rc == ADMM_OK; ++it) {
                 float ms = 0.f;
                 if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = ADMM_ERR_CUDA; break; }
-                branch_tron_kernel<<<nbk, kBranchBlock, 0, h->stream>>>(G, h->O);
+                launch_branch(clan[c], nbk, h->stream, G, h->O);
                 if (cudaEventRecord(e1, h->stream) != cudaSuccess) { rc = ADMM_ERR_CUDA; break; }
                 bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
                 control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);
@@ -1330,11 +1360,13 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
     int best = 0;
     for (int c = 1; c < kCand; ++c)
         if (tot[c] < tot[best]) best = c;
-    const int nbk = cand[best] < need ? (cand[best] > 0 ? cand[best] : 1) : need;
+    const int nbk = blocks_of(best);
     if (rc == ADMM_OK) {
         h->nblk_branch = nbk;
         h->G.nblk_branch = nbk;
         h->opts.branch_blocks = nbk;
+        h->lanes = clan[best];
+        h->opts.lanes_per_branch = clan[best];
     }
     // graph shape: iterations per body of the WHILE node, timed through the
     // graph itself over 4 * iters iterations replayed from the same state
@@ -1390,6 +1422,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
     if (rc != ADMM_OK) return rc;
     if (blocks_out) *blocks_out = nbk;
     if (body_out) *body_out = h->opts.graph_body_iters;
+    if (lanes_out) *lanes_out = h->lanes;
     if (ms_best) *ms_best = tot[best] / (2.0 * iters);
     return ADMM_OK;
 }
@@ -1407,7 +1440,7 @@ extern "C" int admm_profile_iterations(admm_handle *h, int32_t iters, double *ms
     cudaGraphConditionalHandle none = 0;
     CK(cudaEventRecord(ev[0], h->stream));
     for (int it = 0; it < iters; ++it) {
-        branch_tron_kernel<<<h->nblk_branch, kBranchBlock, 0, h->stream>>>(h->G, h->O);
+        launch_branch(h->lanes, h->nblk_branch, h->stream, h->G, h->O);
         CK(cudaEventRecord(ev[2 * it + 1], h->stream));
         bus_dual_kernel<<<h->nblk_bus, kBusBlock, 0, h->stream>>>(h->G, h->O);
         control_kernel<<<1, 32, 0, h->stream>>>(h->G, none, 0);

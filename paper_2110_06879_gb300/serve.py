@@ -50,8 +50,8 @@ class Server:
     `saved_states()`) seeds the pool with solved grids: their states are put
     back whenever they are resident, and none of them is cold-solved on entry
     (`warm_iters` sets the cold-solve length for the others).  `tuned` is a
-    launch shape (branch blocks, iterations per graph body) to use instead of
-    tuning in warm_up."""
+    launch shape (branch blocks, iterations per graph body, ms, lanes per
+    branch), as Solver.autotune returns it, used for every rebuilt handle."""
 
     def __init__(self, grids, mem_budget: int, rho_pq=3e3, rho_va=3e4, tol=1e-3, max_iter=2000,
                  tick_iters=8, stream=None, states=None, tuned=None, warm_iters=None, **opts):
@@ -84,7 +84,8 @@ class Server:
         self.bytes = state_bytes(self.grids)
         extra = {}
         if self.tuned:
-            extra = dict(branch_blocks=self.tuned[0], graph_body_iters=self.tuned[1])
+            extra = dict(branch_blocks=self.tuned[0], graph_body_iters=self.tuned[1],
+                         lanes_per_branch=self.tuned[3])
         self.solver = admm.Solver(self.grids, stream=self.stream, rho_pq=self.rho[0],
                                   rho_va=self.rho[1], **dict(self.opts, **extra))
         for k in self.grid_ids:

@@ -60,15 +60,19 @@ def test_admittance_and_cold_start():
                                              (2, dict(rho_pq=10.0, rho_va=1e3), False),
                                              (3, dict(TINY, two_level=0), False),
                                              (1, TINY, True), (5, TINY, True),
-                                             (7, dict(TINY, beta_rule=1, max_inner=2), False)])
+                                             (7, dict(TINY, beta_rule=1, max_inner=2), False),
+                                             (0, dict(TINY, lanes_per_branch=2), False),
+                                             (5, dict(TINY, lanes_per_branch=2), True)])
 def test_first_ten_iterations(seed, kw, devices):
     """Every iterate of the first ten iterations; devices: bus shunts,
     transformers and phase shifters; beta_rule 1: the adaptive outer penalty,
-    with an outer update every second iteration."""
+    with an outer update every second iteration; lanes_per_branch 2: the
+    branch kernel with a lane pair per branch."""
     grid = synth.tiny_grid(seed, devices=devices)
     s = admm.Solver(grid, **kw)
+    okw = {k: v for k, v in kw.items() if k != "lanes_per_branch"}   # a launch setting
     for k in range(1, 11):
-        o = oracle.Oracle(grid, **kw)
+        o = oracle.Oracle(grid, **okw)
         o.solve(tol=0.0, max_iter=k)
         st = s.solve(tol=0.0, max_iter=k)
         assert st == admm.ADMM_NOT_CONVERGED
@@ -237,15 +241,16 @@ def test_set_loads_device_matches_host():
     assert np.array_equal(a.vector(admm.ADMM_VEC_XBAR), b.vector(admm.ADMM_VEC_XBAR))
 
 
-@pytest.mark.parametrize("nbus,iters,rho,devices", [(2000, 8, None, False),
-                                                    (10000, 6, (3e3, 3e4), False),
-                                                    (2000, 10, (3e3, 3e4), True)])
-def test_medium_grid_full_parity(nbus, iters, rho, devices):
+@pytest.mark.parametrize("nbus,iters,rho,devices,lanes", [(2000, 8, None, False, 1),
+                                                          (10000, 6, (3e3, 3e4), False, 1),
+                                                          (2000, 10, (3e3, 3e4), True, 1),
+                                                          (10000, 6, (3e3, 3e4), False, 2)])
+def test_medium_grid_full_parity(nbus, iters, rho, devices, lanes):
     """Every coupling against the oracle: the 2k grid at Table 1's penalties,
     the 10k tracking grid at the tracking penalties (spanning several branch
-    launches' worth of queue refills), and a 2k grid with bus shunts (10% of
-    buses), transformers (10% of branches) and phase shifters over ten
-    iterations."""
+    launches' worth of queue refills; once more with two lanes per branch),
+    and a 2k grid with bus shunts (10% of buses), transformers (10% of
+    branches) and phase shifters over ten iterations."""
     grid = synth.sized_grid(nbus, seed=11, devices=devices)
     if devices:
         assert np.count_nonzero(grid.gs) > 100 and np.count_nonzero(grid.shift) > 20
@@ -253,11 +258,11 @@ def test_medium_grid_full_parity(nbus, iters, rho, devices):
     if rho is not None:
         rp, rv = rho
     kw = dict(rho_pq=rp, rho_va=rv, obj_scale=so)
-    s = admm.Solver(grid, **kw)
+    s = admm.Solver(grid, lanes_per_branch=lanes, **kw)
     o = oracle.Oracle(grid, **kw)
     s.solve(tol=0.0, max_iter=iters)
     o.solve(tol=0.0, max_iter=iters)
-    compare_state(s, o, 1e-9, f"{nbus}")
+    compare_state(s, o, 1e-9, f"{nbus} lanes {lanes}")
 
 
 def test_full_size_70k_sampled():

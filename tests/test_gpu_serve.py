@@ -27,7 +27,7 @@ def test_served_results_equal_solo_replay():
     reqs = serve.poisson_requests(grids, rate=400.0, duration=0.05, seed=3)
     assert len(reqs) >= 6
     srv = serve.Server(grids, mem_budget=1 << 30, tol=1e-4, max_iter=300, tick_iters=4, **KW)
-    srv.warm_up(max_iter=300)
+    srv.warm_up(max_iter=300, tune=False)   # bitwise replay: the same launch shape as solo
     recs, rejected, wall = srv.run(reqs)
     assert not rejected and len(recs) == len(reqs)
     for k, g in enumerate(grids):
@@ -83,7 +83,7 @@ def test_memory_budget_swaps_grids_in_and_out():
     assert serve.state_bytes(grids) > budget >= serve.state_bytes([grids[1], grids[2]])
     srv = serve.Server(grids, mem_budget=budget, tol=1e-4, max_iter=200, tick_iters=4, **KW)
     assert srv.grid_ids == [0, 1]
-    srv.warm_up(max_iter=300)
+    srv.warm_up(max_iter=300, tune=False)   # bitwise replay: the same launch shape as solo
     reqs = serve.poisson_requests(grids, rate=300.0, duration=0.06, seed=4)
     assert {r.grid for r in reqs} == {0, 1, 2}
     recs, rejected, _ = srv.run(reqs)

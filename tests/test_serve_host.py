@@ -57,7 +57,7 @@ class FakeSolver:
         pass
 
     def autotune(self, iters):
-        return (1, 1, 0.1)
+        return (1, 1, 0.1, 1)
 
     def get_scenario_state(self, s):
         return (self.grids[s].gid, self.solves[s])
