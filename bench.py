@@ -60,8 +60,8 @@ def algorithmic_flops(stats: dict) -> float:
 # aside) is the one the counters were taken on; any change to it makes the
 # figure stale (null).
 TRAFFIC_CAPTURE = {"nbus": 70000, "seed": 1,
-                   "source_digest": "89b7d6b2b497c785018e414c1989d43647a243b7d3bfc0921cf1b3da7ad4f969",
-                   "bytes_per_launch": 22.303744e6 + 0.549376e6}
+                   "source_digest": "87890a59bb37a9def435401c4dfecb28d24af3130afe940126076bc0275bce80",
+                   "bytes_per_launch": 22.302720e6 + 0.510464e6}
 
 
 def kernel_source_digest(path):
@@ -697,6 +697,7 @@ def run_ours(args):
         tgrid = synth.sized_grid(10000, seed=args.seed + 100 + rank)
         topts = dict(rho_pq=3e3, rho_va=3e4, obj_scale=1.0)
         ts = admm.Solver(tgrid, stream=stream, **topts)
+        tuned_t = ts.autotune(2)        # launch shape for this grid (state put back)
         pds, qds = synth.ar1_loads(tgrid, args.track_steps, seed=args.seed + 200 + rank)
         pmaxs = tracking.renewable_pmax(tgrid, args.track_steps, seed=args.seed + 300 + rank)
         cold, recs = tracking.run_tracking(ts, tgrid, pds, qds, pmaxs, tol=1e-3, max_iter=5000,
@@ -706,7 +707,9 @@ def run_ours(args):
                                   f"{tgrid.ngen} generators), AR(1) loads phi 0.9 noise 1%, 20% "
                                   "renewable p_max ramps +-3%, ramp limit 2% p_max, warm starts",
                       "rho_pq": topts["rho_pq"], "rho_va": topts["rho_va"], "tol": 1e-3,
-                      "stop_rule": STOP_RULE})
+                      "stop_rule": STOP_RULE, "autotuned_branch_blocks": tuned_t[0],
+                      "autotuned_graph_body_iters": tuned_t[1],
+                      "autotuned_lanes_per_branch": tuned_t[3]})
         ts.close()
 
     batched = run_batched(args, admm, stream, device=dev) if args.batched > 0 else None
