@@ -17,10 +17,10 @@
 // from a queue as soon as its branch is finished; each trip of the main loop
 // performs exactly one TRON iteration in every lane that has one to do, so the
 // expensive code runs with nearly full warps.  One lane solves one branch
-// (its Hessian packed, 21 entries, in shared memory, everything else in
-// registers; the TRON free set handled with masks so all loops have fixed trip
-// counts); the branch data the evaluations read (admittances and targets) sit
-// in shared memory too.  The function, gradient and Hessian are evaluated
+// (its Hessian and preconditioner factor packed, 21 entries each, in shared
+// memory, everything else in registers; the TRON free set handled with masks
+// so all loops have fixed trip counts); the branch data the evaluations read
+// (admittances and targets) sit in shared memory too.  The function, gradient and Hessian are evaluated
 // together at every trial point (one sincos), since nearly every trial step is
 // accepted; after a rejected step the gradient and Hessian are re-evaluated at
 // the kept point.
@@ -40,10 +40,10 @@ __host__ __device__ constexpr int P(int i, int j)
     return i <= j ? (i * (11 - i)) / 2 + j : (j * (11 - j)) / 2 + i;
 }
 
-// A lane's packed symmetric Hessian lives in shared memory, the block's lanes
-// interleaved (stride kBranchBlock): held in registers it costs 42 of the 255
-// a lane has, and the subspace step then spills; from shared memory the
-// 70,000-bus launch ran 6 % faster.
+// A lane's packed symmetric matrices (the Hessian, the preconditioner's
+// factor and the scaled matrix it factors) live in shared memory, the block's
+// lanes interleaved (stride kBranchBlock): held in registers each costs 42 of
+// the 255 a lane has, and the subspace step then spills.
 struct SMat {
     double *p;
     __device__ __forceinline__ double &operator[](int k) const { return p[k * kBranchBlock]; }
@@ -547,45 +547,64 @@ __device__ __forceinline__ double boundary_tau(const double *a, const double *pv
     return dpos(ap) ? rad / (ap + disc) : (disc - ap) / pp;
 }
 
-// one Cholesky pass of D^-1 A D^-1 + sigma I on the free block (identity on
-// fixed variables); the diagonal of L keeps the reciprocal pivots.  Lanes
-// with keep == true leave L unchanged.  kPlain: D = I and sigma = 0.
+// One Cholesky pass of M + sigma I on the free block (identity on fixed
+// variables), M = H (kPlain, sigma = 0) or the scaled matrix D^-1 H D^-1; the
+// diagonal of the factor keeps the reciprocal pivots.  The pass runs in
+// registers; lanes with write == true store the factor to L.
 template <bool kPlain>
-__device__ __forceinline__ bool chol_pass(SMat H, const bool *fr, const double *dinv,
-                                          double sigma, bool keep, double *L)
+__device__ __forceinline__ bool chol_pass(SMat M, const bool *fr, double sigma, bool write, SMat L)
 {
+    double l[21];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double dd = fr[j] ? (kPlain ? H[P(j, j)] : H[P(j, j)] * dinv[j] * dinv[j] + sigma) : 1.0;
+        double dd = fr[j] ? (kPlain ? M[P(j, j)] : M[P(j, j)] + sigma) : 1.0;
 #pragma unroll
-        for (int k = 0; k < j; ++k) dd -= L[P(j, k)] * L[P(j, k)];
+        for (int k = 0; k < j; ++k) dd -= l[P(j, k)] * l[P(j, k)];
         ok = ok && dpos(dd);
         const double linv = rsqrt(dmaxi(dd, 1e-300));
-        L[P(j, j)] = keep ? L[P(j, j)] : linv;
+        l[P(j, j)] = linv;
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            double v = (fr[i] && fr[j]) ? (kPlain ? H[P(i, j)] : H[P(i, j)] * dinv[i] * dinv[j]) : 0.0;
+            double v = (fr[i] && fr[j]) ? M[P(i, j)] : 0.0;
 #pragma unroll
-            for (int k = 0; k < j; ++k) v -= L[P(i, k)] * L[P(j, k)];
-            L[P(i, j)] = keep ? L[P(i, j)] : v * linv;
+            for (int k = 0; k < j; ++k) v -= l[P(i, k)] * l[P(j, k)];
+            l[P(i, j)] = v * linv;
         }
+    }
+    if (write) {
+#pragma unroll
+        for (int k = 0; k < 21; ++k) L[k] = l[k];
     }
     return ok;
 }
 
+// k-th shift of the schedule sigma_0 = (pos ? 0 : 1e-3),
+// sigma_{t+1} = max(2 sigma_t, 1e-3): 1e-3 * 2^(k - pos), or 0 at k = 0 when
+// pos.  Doubling is exact, so adding to the exponent gives the doubled value
+// bit for bit.
+__device__ __forceinline__ double shift_at(int k, bool pos)
+{
+    const int e = pos ? k - 1 : k;
+    return e < 0 ? 0.0 : __longlong_as_double(__double_as_longlong(1e-3) + ((long long)e << 52));
+}
+
 // Preconditioner: Cholesky factor of D^-1 A D^-1 + sigma I on the free block,
-// D = diag(sqrt|A_ii|), sigma = 0 if every free A_ii > 0 else 1e-3, doubled
-// until the factorisation succeeds (at most kCholTries passes).  A positive
+// D = diag(sqrt|A_ii|), sigma the first shift of the schedule above (at most
+// kCholTries of them) for which the factorisation succeeds.  A positive
 // definite block is first factored unscaled: then D L L' D = L0 L0' exactly,
-// so the preconditioned CG iterates are the same.
-__device__ __forceinline__ void precond_factor(bool on, SMat H, const bool *fr, double *L,
+// so the preconditioned CG iterates are the same.  The first successful shift
+// is found by bisection over the schedule's indices (about 5 factorisations
+// instead of up to 20 in sequence): A + sigma I stays positive definite as
+// sigma grows, so success is monotone in the index and bisection finds the
+// same shift as trying the shifts in order.  S holds the scaled matrix.
+__device__ __forceinline__ void precond_factor(bool on, SMat H, SMat S, const bool *fr, SMat L,
                                                double *dinv)
 {
 #pragma unroll
     for (int i = 0; i < 6; ++i) dinv[i] = 1.0;
-    const bool plain = chol_pass<true>(H, fr, dinv, 0.0, false, L);
-    bool need = on && !plain;
+    const bool plain = chol_pass<true>(H, fr, 0.0, true, L);
+    const bool need = on && !plain;
     if (!__any_sync(kFull, need)) return;
     bool pos = true;
     double ds[6];
@@ -596,25 +615,40 @@ __device__ __forceinline__ void precond_factor(bool on, SMat H, const bool *fr, 
         pos = pos && (!fr[i] || dpos(a));
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dinv[i] = need ? ds[i] : dinv[i];
-    double sigma = pos ? 0.0 : 1e-3;
-    for (int tries = 0; tries < kCholTries; ++tries) {
-        if (!__any_sync(kFull, need)) break;
-        const bool ok = chol_pass<false>(H, fr, dinv, sigma, !need, L);
-        need = need && !ok;
-        sigma = dmaxi(sigma * 2.0, 1e-3);
+    for (int i = 0; i < 6; ++i) {
+        dinv[i] = need ? ds[i] : dinv[i];
+#pragma unroll
+        for (int j = i; j < 6; ++j)
+            if (need) S[P(i, j)] = H[P(i, j)] * ds[i] * ds[j];
     }
-    if (__any_sync(kFull, need)) {   // give up: identity in the scaled space
+    // first success in [lo, hi]; hi == kCholTries: none found yet.  `held`:
+    // L holds the factor at hi (the lane's last pass succeeded)
+    int lo = 0, hi = kCholTries;
+    bool srch = need, held = false;
+    for (int t = 0; t < 8; ++t) {
+        if (!__any_sync(kFull, srch)) break;
+        const int mid = (lo + hi) >> 1;
+        const bool ok = chol_pass<false>(S, fr, shift_at(mid, pos), srch, L);
+        if (srch) {
+            hi = ok ? mid : hi;
+            lo = ok ? lo : mid + 1;
+            held = ok;
+        }
+        srch = srch && lo < hi;
+    }
+    const bool redo = need && hi < kCholTries && !held;
+    if (__any_sync(kFull, redo)) chol_pass<false>(S, fr, shift_at(hi, pos), redo, L);
+    if (__any_sync(kFull, need && hi >= kCholTries)) {   // give up: identity in the scaled space
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
 #pragma unroll
-            for (int j = 0; j <= i; ++j) L[P(i, j)] = need ? ((i == j) ? 1.0 : 0.0) : L[P(i, j)];
+            for (int j = 0; j <= i; ++j)
+                if (need && hi >= kCholTries) L[P(i, j)] = (i == j) ? 1.0 : 0.0;
         }
     }
 }
 
-__device__ __forceinline__ void precond_solve(const double *L, const double *dinv, const double *r,
-                                              double *z)
+__device__ __forceinline__ void precond_solve(SMat L, const double *dinv, const double *r, double *z)
 {
     double t[6];
 #pragma unroll
@@ -639,7 +673,7 @@ __device__ __forceinline__ void precond_solve(const double *L, const double *din
 // a projected backtracking search along the CG direction.
 template <int kL>
 __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double *x, const double *g,
-                                         SMat H, double d2, const double *sc, double qc,
+                                         SMat H, SMat L, SMat S, double d2, const double *sc, double qc,
                                          double *s, double &qs, Cnt &c)
 {
     qs = qc;                 // q(s) for the step returned: the Cauchy point's, or
@@ -660,8 +694,8 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     hmul<kL>(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
-    double L[21], dinv[6];
-    precond_factor(act, H, fr, L, dinv);
+    double dinv[6];
+    precond_factor(act, H, S, fr, L, dinv);
     // hwb: H times the boundary step tau p, which CG adds to w without
     // updating r; elsewhere H w = r0 - r on the free variables (r0 = -gc)
     double w[6], r[6], z[6], pv[6], q[6], hwb[6];
@@ -827,10 +861,13 @@ enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE =
 template <int kL>
 __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
 {
-    __shared__ double sh[16 * kBranchBlock];   // per lane: Y[8], t[8], stride kBranchBlock
+    // dynamic shared memory, per lane with stride kBranchBlock: Y[8], t[8],
+    // then the packed Hessian, the preconditioner's factor and scaled matrix
+    extern __shared__ double sh[];
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
-    __shared__ double shH[21 * kBranchBlock];  // per lane: packed Hessian
-    const SMat H{shH + threadIdx.x};
+    const SMat H{sh + 16 * kBranchBlock + threadIdx.x};
+    const SMat Lf{sh + 37 * kBranchBlock + threadIdx.x};
+    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
@@ -887,7 +924,7 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
             double sc[6], s[6];
             double qs = 0.0, qsc = 0.0;
             cauchy<kL>(go_t, B, x, g, H, dsq, alpha, sc, qsc, c);
-            subspace<kL>(go_t, B, x, g, H, dsq, sc, qsc, s, qs, c);
+            subspace<kL>(go_t, B, x, g, H, Lf, Sc, dsq, sc, qsc, s, qs, c);
             const double s2 = dot6<kL>(s, s);
             if (go_t) {
                 double xn = 0.0, sn = 0.0;

@@ -315,8 +315,16 @@ void *branch_func(int lanes)
 
 void launch_branch(int lanes, int nbk, cudaStream_t s, const DevGrid &G, const DevOpts &O)
 {
-    if (lanes == 2) branch_tron2_kernel<<<nbk, kBranchBlock, 0, s>>>(G, O);
-    else branch_tron_kernel<<<nbk, kBranchBlock, 0, s>>>(G, O);
+    if (lanes == 2) branch_tron2_kernel<<<nbk, kBranchBlock, kBranchSmem, s>>>(G, O);
+    else branch_tron_kernel<<<nbk, kBranchBlock, kBranchSmem, s>>>(G, O);
+}
+
+// the branch kernels take more than the default 48 KB of dynamic shared memory
+int branch_smem_setup()
+{
+    for (void *f : {(void *)branch_tron_kernel, (void *)branch_tron2_kernel})
+        CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBranchSmem));
+    return ADMM_OK;
 }
 
 // blocks that give every branch a slot (128 / lanes slots per block)
@@ -376,6 +384,7 @@ int build_graph(admm_handle *h)
     bp.func = branch_func(h->lanes);
     bp.gridDim = dim3(h->nblk_branch);
     bp.blockDim = dim3(kBranchBlock);
+    bp.sharedMemBytes = (unsigned)kBranchSmem;
     bp.kernelParams = bargs;
     cudaKernelNodeParams up{};
     up.func = (void *)bus_dual_kernel;
@@ -582,6 +591,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     // device layout
     const Layout Lo = layout_of(zs);
     h->dbytes = Lo.bytes;
+    if ((rc = branch_smem_setup()) != ADMM_OK) { delete h; return rc; }
     cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
     if (e != cudaSuccess) {
         set_err("cudaMalloc(%zu) failed: %s", h->dbytes, cudaGetErrorString(e));
@@ -968,7 +978,7 @@ extern "C" int admm_get_vector(admm_handle *h, int32_t which, double *out)
     if (!h || !out) { set_err("NULL argument"); return ADMM_ERR_INVALID_ARG; }
     const int nb = h->nb, nl = h->nl, ng = h->ng, ns = h->ns;
     const Range R = range_of(h, h->sel);
-    const int nls = R.b1 - R.b0, ngs = R.g1 - R.g0, nbs = R.i1 - R.i0;
+    const int ngs = R.g1 - R.g0, nbs = R.i1 - R.i0;
     std::vector<double> a, b, c;
     int rc = ADMM_OK;
     // canonical order within the scenario: its generators, then its branches
