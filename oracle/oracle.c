@@ -745,16 +745,18 @@ static void update_generators(ora *p)
 
 /* rho-tilde at the start of a branch solve (reading of this implementation;
  * Section II-C gives no schedule): al_rho0 when set, else
- * rho_pq / (2 rbar)^2 with rbar the tightened rating, i.e. the penalty
- * rt/2 h^2 on h = p^2 + q^2 + s weighs a deviation dS of the apparent flow
- * at the limit (dh = 2 rbar dS) like the coupling penalty rho_pq/2 dS^2
+ * 25 rho_pq / rbar^2 with rbar the tightened rating: 100 times the penalty
+ * rho_pq / (2 rbar)^2 under which rt/2 h^2 on h = p^2 + q^2 + s weighs a
+ * deviation dS of the apparent flow at the limit (dh = 2 rbar dS) like the
+ * coupling penalty rho_pq/2 dS^2 -- one growth step ahead, since the first
+ * passes at that weight seldom cut the violation enough to avoid the growth
  * (capped at al_rho_max); rho_pq for a line without a limit. */
 static double al_rho_start(const ora *p, int l)
 {
     if (p->o.al_rho0 > 0.0) return p->o.al_rho0;
     double rb2 = -s_lower(p, l);
     if (!(rb2 < 1e19)) return p->o.rho_pq;
-    double r = p->o.rho_pq / (4.0 * rb2);
+    double r = 25.0 * p->o.rho_pq / rb2;
     return r < p->o.al_rho_max ? r : p->o.al_rho_max;
 }
 

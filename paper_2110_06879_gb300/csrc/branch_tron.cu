@@ -175,7 +175,10 @@ __device__ __forceinline__ void flow_end(bool od, double a, double al, double be
 }
 
 // f, gradient, packed Hessian and the four flows of eq. branch at x.
-// Y and t live in shared memory with stride kBranchBlock.
+// Y and t live in shared memory with stride kBranchBlock.  The flow values
+// come first (h and the multipliers mu need all four); each flow's
+// derivatives are then formed and summed one flow at a time, which keeps
+// fewer values live than forming all four first.
 __device__ __forceinline__ void evaluate1(const double *sY, const double *sT, double rpq, double rva,
                                           double lt0, double lt1, double rt, const double *x,
                                           double &f, double *g, SMat H, double *F)
@@ -185,43 +188,55 @@ __device__ __forceinline__ void evaluate1(const double *sY, const double *sT, do
     sincos(x[2] - x[3], &s, &c);
     const double vv = vi * vj;
     constexpr int S = kBranchBlock;
+    // flow k: a_k v_self^2 + v_i v_j (al_k cos th + be_k sin th);
+    // p_ij, q_ij (self v_i), p_ji, q_ji (self v_j), eqs. (pij)-(qji)
     const double gii = sY[0 * S], bii = sY[1 * S], gij = sY[2 * S], bij = sY[3 * S];
     const double gji = sY[4 * S], bji = sY[5 * S], gjj = sY[6 * S], bjj = sY[7 * S];
-    Flow fl[4];
-    flow<true>(gii, gij, bij, vi, vj, vv, c, s, fl[0]);      // p_ij eq. (pij)
-    flow<true>(-bii, -bij, gij, vi, vj, vv, c, s, fl[1]);    // q_ij eq. (qij)
-    flow<false>(gjj, gji, -bji, vi, vj, vv, c, s, fl[2]);    // p_ji eq. (pji)
-    flow<false>(-bjj, -bji, -gji, vi, vj, vv, c, s, fl[3]);  // q_ji eq. (qji)
-    const double h0 = fl[0].F * fl[0].F + fl[1].F * fl[1].F + x[4];
-    const double h1 = fl[2].F * fl[2].F + fl[3].F * fl[3].F + x[5];
+    const double fa[4] = {gii, -bii, gjj, -bjj};
+    const double fal[4] = {gij, -bij, gji, -bji};
+    const double fbe[4] = {bij, gij, -bji, -gji};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double vk = k < 2 ? vi : vj;
+        F[k] = fa[k] * vk * vk + vv * (fal[k] * c + fbe[k] * s);
+    }
+    const double h0 = F[0] * F[0] + F[1] * F[1] + x[4];
+    const double h1 = F[2] * F[2] + F[3] * F[3] + x[5];
     const double mu0 = lt0 + rt * h0, mu1 = lt1 + rt * h1;
     double G0 = 0.0, G1 = 0.0, G2 = 0.0, fq = 0.0;
     double A00 = 0.0, A11 = 0.0, A01 = 0.0, A02 = 0.0, A12 = 0.0, A22 = 0.0;
+    // halves of the gradients of h_e in (v_i, v_j, th): sum_k F_k dF_k
+    double e00 = 0.0, e01 = 0.0, e02 = 0.0, e10 = 0.0, e11 = 0.0, e12 = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+        Flow fl;
+        if (k < 2) flow<true>(fa[k], fal[k], fbe[k], vi, vj, vv, c, s, fl);
+        else flow<false>(fa[k], fal[k], fbe[k], vi, vj, vv, c, s, fl);
         const double mu = k < 2 ? mu0 : mu1;
-        const double r = fl[k].F - sT[k * S];
+        const double r = F[k] - sT[k * S];
         fq += r * r;
-        const double ck = rpq * r + 2.0 * mu * fl[k].F;
+        const double ck = rpq * r + 2.0 * mu * F[k];
         const double wk = rpq + 2.0 * mu;
-        G0 += ck * fl[k].d0;
-        G1 += ck * fl[k].d1;
-        G2 += ck * fl[k].d2;
-        A00 += ck * fl[k].h00 + wk * fl[k].d0 * fl[k].d0;
-        A11 += ck * fl[k].h11 + wk * fl[k].d1 * fl[k].d1;
-        A01 += ck * fl[k].h01 + wk * fl[k].d0 * fl[k].d1;
-        A02 += ck * fl[k].h02 + wk * fl[k].d0 * fl[k].d2;
-        A12 += ck * fl[k].h12 + wk * fl[k].d1 * fl[k].d2;
-        A22 += ck * fl[k].h22 + wk * fl[k].d2 * fl[k].d2;
-        F[k] = fl[k].F;
+        G0 += ck * fl.d0;
+        G1 += ck * fl.d1;
+        G2 += ck * fl.d2;
+        A00 += ck * fl.h00 + wk * fl.d0 * fl.d0;
+        A11 += ck * fl.h11 + wk * fl.d1 * fl.d1;
+        A01 += ck * fl.h01 + wk * fl.d0 * fl.d1;
+        A02 += ck * fl.h02 + wk * fl.d0 * fl.d2;
+        A12 += ck * fl.h12 + wk * fl.d1 * fl.d2;
+        A22 += ck * fl.h22 + wk * fl.d2 * fl.d2;
+        if (k < 2) {
+            e00 += F[k] * fl.d0;
+            e01 += F[k] * fl.d1;
+            e02 += F[k] * fl.d2;
+        } else {
+            e10 += F[k] * fl.d0;
+            e11 += F[k] * fl.d1;
+            e12 += F[k] * fl.d2;
+        }
     }
-    // gradients of h_e in (v_i, v_j, th)
-    const double e00 = 2.0 * (fl[0].F * fl[0].d0 + fl[1].F * fl[1].d0);
-    const double e01 = 2.0 * (fl[0].F * fl[0].d1 + fl[1].F * fl[1].d1);
-    const double e02 = 2.0 * (fl[0].F * fl[0].d2 + fl[1].F * fl[1].d2);
-    const double e10 = 2.0 * (fl[2].F * fl[2].d0 + fl[3].F * fl[3].d0);
-    const double e11 = 2.0 * (fl[2].F * fl[2].d1 + fl[3].F * fl[3].d1);
-    const double e12 = 2.0 * (fl[2].F * fl[2].d2 + fl[3].F * fl[3].d2);
+    e00 *= 2.0; e01 *= 2.0; e02 *= 2.0; e10 *= 2.0; e11 *= 2.0; e12 *= 2.0;
     A00 += rt * (e00 * e00 + e10 * e10);
     A11 += rt * (e01 * e01 + e11 * e11);
     A01 += rt * (e00 * e01 + e10 * e11);
@@ -1037,12 +1052,13 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
                         B.vhi_j = G.lim[3 * nl + b];
                         B.slo = G.lim[4 * nl + b];
                         B.set_keys();
-                        // rho-tilde starts at rho_pq / (2 rbar)^2: the penalty on
-                        // h = p^2 + q^2 + s weighs a flow deviation at the limit
-                        // like the coupling penalty does (rho_pq without a limit)
+                        // rho-tilde starts at 25 rho_pq / rbar^2: 100 times the
+                        // penalty on h = p^2 + q^2 + s that weighs a flow deviation
+                        // at the limit like the coupling penalty does (rho_pq
+                        // without a limit)
                         {
                             const double rb2 = -B.slo;
-                            const double r = rpq / (4.0 * rb2);
+                            const double r = 25.0 * rpq / rb2;
                             rt0 = O.al_rho0 > 0.0 ? O.al_rho0
                                 : (rb2 < 1e19 ? (r < O.al_rho_max ? r : O.al_rho_max) : rpq);
                         }
