@@ -100,7 +100,8 @@ typedef struct {
     int32_t al_max_iter;   /* 20 */
     int32_t tron_max_iter; /* 200 */
     int32_t use_graph;     /* 1: conditional-WHILE CUDA graph; 0: stream launches   */
-    int32_t branch_blocks; /* resident blocks of 128 branch lanes; 0: one per SM       */
+    int32_t branch_blocks; /* resident blocks of 128 branch lanes; 0: two per SM when the
+                              branches fill them, else one per SM              */
     int32_t graph_body_iters; /* iterations per body of the WHILE node, 1..16 (1); the
                                  loop still stops after exactly the iteration that
                                  converges or reaches max_iter                       */

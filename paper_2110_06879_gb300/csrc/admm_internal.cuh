@@ -130,7 +130,7 @@ __global__ void finalize_kernel(DevGrid G, Range R, double *pg, double *qg, doub
                                 int32_t nblk);
 
 constexpr int kBranchBlock = 128;
-constexpr int kBranchBlocksPerSM = 1;
+constexpr int kBranchBlocksPerSM = 1;   // launch bound: 255 registers a lane (two blocks still fit an SM)
 // dynamic shared memory of a branch_tron block: per lane, the branch data
 // (Y[8], t[8]), the packed Hessian, the preconditioner's packed factor and the
 // scaled matrix it factors (21 doubles each)

@@ -128,57 +128,62 @@ struct Bounds {
     __device__ __forceinline__ bool below_hi(int i, double v) const { return okey(v) < khi(i); }
 };
 
-// One flow a_self v_k^2 + v_i v_j (alpha cos th + beta sin th): value, gradient
-// in (v_i, v_j, th) and Hessian entries (ii, jj, ij, i-th, j-th, th-th).
-struct Flow {
-    double F, d0, d1, d2, h00, h11, h01, h02, h12, h22;
+// One line end's two flows p and q.  A flow is a v_k^2 + v_i v_j T(th) with
+// T = al cos th + be sin th, T' = dT/dth = be cos th - al sin th; an end's q
+// flow has the angle factors (Tq, Tq') = (-sg T', sg T) of its p flow's, with
+// sg = +1 at the from end and -1 at the to end, so the pair shares the six
+// products of (v_j, v_i, v_i v_j) with (T, T').  Adds the end's terms to the
+// gradient and Hessian sums (ck = rho_pq r + 2 mu F and wk = rho_pq + 2 mu per
+// flow, mu = lt + rt h of the end) and returns the end's halves of
+// grad h = 2 sum F dF in e0..e2.  from: the from end (self term in v_i); a
+// constant for one lane per branch, the lane's end (a selection, not a branch
+// of the code) for two.
+struct EndSums {
+    double G0, G1, G2, A00, A11, A01, A02, A12, A22, fq;
 };
 
-template <bool kSelfI>
-__device__ __forceinline__ void flow(double a, double al, double be, double vi, double vj,
-                                     double vv, double c, double s, Flow &o)
+__device__ __forceinline__ void end_terms(bool from, double ap, double aq, double vi, double vj, double vv,
+                                          double T, double Tp, double Fp, double Fq, double tp,
+                                          double tq, double rpq, double mu, EndSums &E,
+                                          double &e0, double &e1, double &e2)
 {
-    const double T = al * c + be * s;
-    const double Tp = be * c - al * s;
-    const double vk = kSelfI ? vi : vj;
-    o.F = a * vk * vk + vv * T;
-    o.d0 = (kSelfI ? 2.0 * a * vi : 0.0) + vj * T;
-    o.d1 = (kSelfI ? 0.0 : 2.0 * a * vj) + vi * T;
-    o.d2 = vv * Tp;
-    o.h00 = kSelfI ? 2.0 * a : 0.0;
-    o.h11 = kSelfI ? 0.0 : 2.0 * a;
-    o.h01 = T;
-    o.h02 = vj * Tp;
-    o.h12 = vi * Tp;
-    o.h22 = -vv * T;
-}
-
-// One flow of either end (od: the to end, whose self term is in v_j), as
-// flow<true> / flow<false> with the choice made by selection, not a branch.
-__device__ __forceinline__ void flow_end(bool od, double a, double al, double be, double vi,
-                                         double vj, double vv, double c, double s, Flow &o)
-{
-    const double T = al * c + be * s;
-    const double Tp = be * c - al * s;
-    const double vk = od ? vj : vi;
-    const double ds = 2.0 * a * vk;
-    o.F = a * vk * vk + vv * T;
-    o.d0 = (od ? 0.0 : ds) + vj * T;
-    o.d1 = (od ? ds : 0.0) + vi * T;
-    o.d2 = vv * Tp;
-    o.h00 = od ? 0.0 : 2.0 * a;
-    o.h11 = od ? 2.0 * a : 0.0;
-    o.h01 = T;
-    o.h02 = vj * Tp;
-    o.h12 = vi * Tp;
-    o.h22 = -vv * T;
+    const double jT = vj * T, iT = vi * T, vT = vv * T;
+    const double jP = vj * Tp, iP = vi * Tp, vP = vv * Tp;
+    // the q flow's v_j Tq, v_i Tq, vv Tq and v_j Tq', v_i Tq', vv Tq'
+    const double Tq = from ? -Tp : Tp;
+    const double jTq = from ? -jP : jP, iTq = from ? -iP : iP, vTq = from ? -vP : vP;
+    const double jPq = from ? jT : -jT, iPq = from ? iT : -iT, vPq = from ? vT : -vT;
+    const double vk = from ? vi : vj;
+    const double m2 = 2.0 * mu, wk = rpq + m2;
+    // dF = (2a v_i + v_j T, v_i T, vv T') (from end) or (v_j T, 2a v_j + v_i T, vv T');
+    // d2F: self term 2a, (0,1) T, (0,2) v_j T', (1,2) v_i T', (2,2) -vv T
+    const double dp0 = from ? 2.0 * ap * vk + jT : jT;
+    const double dp1 = from ? iT : 2.0 * ap * vk + iT;
+    const double dq0 = from ? 2.0 * aq * vk + jTq : jTq;
+    const double dq1 = from ? iTq : 2.0 * aq * vk + iTq;
+    const double dp2 = vP, dq2 = vPq;
+    const double rp = Fp - tp, rq = Fq - tq;
+    E.fq += rp * rp + rq * rq;
+    const double cp = rpq * rp + m2 * Fp, cq = rpq * rq + m2 * Fq;
+    E.G0 += cp * dp0 + cq * dq0;
+    E.G1 += cp * dp1 + cq * dq1;
+    E.G2 += cp * dp2 + cq * dq2;
+    const double sd = 2.0 * (cp * ap + cq * aq);         // c times the self second derivative
+    if (from) E.A00 += sd; else E.A11 += sd;
+    E.A00 += wk * (dp0 * dp0 + dq0 * dq0);
+    E.A11 += wk * (dp1 * dp1 + dq1 * dq1);
+    E.A01 += (cp * T + cq * Tq) + wk * (dp0 * dp1 + dq0 * dq1);
+    E.A02 += (cp * jP + cq * jPq) + wk * (dp0 * dp2 + dq0 * dq2);
+    E.A12 += (cp * iP + cq * iPq) + wk * (dp1 * dp2 + dq1 * dq2);
+    E.A22 += -(cp * vT + cq * vTq) + wk * (dp2 * dp2 + dq2 * dq2);
+    e0 = 2.0 * (Fp * dp0 + Fq * dq0);
+    e1 = 2.0 * (Fp * dp1 + Fq * dq1);
+    e2 = 2.0 * (Fp * dp2 + Fq * dq2);
 }
 
 // f, gradient, packed Hessian and the four flows of eq. branch at x.
 // Y and t live in shared memory with stride kBranchBlock.  The flow values
-// come first (h and the multipliers mu need all four); each flow's
-// derivatives are then formed and summed one flow at a time, which keeps
-// fewer values live than forming all four first.
+// come first (h and the multipliers mu need all four), then each end's terms.
 __device__ __forceinline__ void evaluate1(const double *sY, const double *sT, double rpq, double rva,
                                           double lt0, double lt1, double rt, const double *x,
                                           double &f, double *g, SMat H, double *F)
@@ -188,89 +193,64 @@ __device__ __forceinline__ void evaluate1(const double *sY, const double *sT, do
     sincos(x[2] - x[3], &s, &c);
     const double vv = vi * vj;
     constexpr int S = kBranchBlock;
-    // flow k: a_k v_self^2 + v_i v_j (al_k cos th + be_k sin th);
-    // p_ij, q_ij (self v_i), p_ji, q_ji (self v_j), eqs. (pij)-(qji)
     const double gii = sY[0 * S], bii = sY[1 * S], gij = sY[2 * S], bij = sY[3 * S];
     const double gji = sY[4 * S], bji = sY[5 * S], gjj = sY[6 * S], bjj = sY[7 * S];
-    const double fa[4] = {gii, -bii, gjj, -bjj};
-    const double fal[4] = {gij, -bij, gji, -bji};
-    const double fbe[4] = {bij, gij, -bji, -gji};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const double vk = k < 2 ? vi : vj;
-        F[k] = fa[k] * vk * vk + vv * (fal[k] * c + fbe[k] * s);
-    }
+    // eqs. (pij)-(qji): p_ij = g_ii v_i^2 + vv T_i, q_ij = -b_ii v_i^2 - vv T'_i with
+    // (al, be) = (g_ij, b_ij); p_ji = g_jj v_j^2 + vv T_j, q_ji = -b_jj v_j^2 + vv T'_j
+    // with (al, be) = (g_ji, -b_ji)
+    const double Ti = gij * c + bij * s, Tpi = bij * c - gij * s;
+    const double Tj = gji * c - bji * s, Tpj = -bji * c - gji * s;
+    const double wi = vi * vi, wj = vj * vj;
+    F[0] = gii * wi + vv * Ti;
+    F[1] = -bii * wi - vv * Tpi;
+    F[2] = gjj * wj + vv * Tj;
+    F[3] = -bjj * wj + vv * Tpj;
     const double h0 = F[0] * F[0] + F[1] * F[1] + x[4];
     const double h1 = F[2] * F[2] + F[3] * F[3] + x[5];
     const double mu0 = lt0 + rt * h0, mu1 = lt1 + rt * h1;
-    double G0 = 0.0, G1 = 0.0, G2 = 0.0, fq = 0.0;
-    double A00 = 0.0, A11 = 0.0, A01 = 0.0, A02 = 0.0, A12 = 0.0, A22 = 0.0;
-    // halves of the gradients of h_e in (v_i, v_j, th): sum_k F_k dF_k
-    double e00 = 0.0, e01 = 0.0, e02 = 0.0, e10 = 0.0, e11 = 0.0, e12 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        Flow fl;
-        if (k < 2) flow<true>(fa[k], fal[k], fbe[k], vi, vj, vv, c, s, fl);
-        else flow<false>(fa[k], fal[k], fbe[k], vi, vj, vv, c, s, fl);
-        const double mu = k < 2 ? mu0 : mu1;
-        const double r = F[k] - sT[k * S];
-        fq += r * r;
-        const double ck = rpq * r + 2.0 * mu * F[k];
-        const double wk = rpq + 2.0 * mu;
-        G0 += ck * fl.d0;
-        G1 += ck * fl.d1;
-        G2 += ck * fl.d2;
-        A00 += ck * fl.h00 + wk * fl.d0 * fl.d0;
-        A11 += ck * fl.h11 + wk * fl.d1 * fl.d1;
-        A01 += ck * fl.h01 + wk * fl.d0 * fl.d1;
-        A02 += ck * fl.h02 + wk * fl.d0 * fl.d2;
-        A12 += ck * fl.h12 + wk * fl.d1 * fl.d2;
-        A22 += ck * fl.h22 + wk * fl.d2 * fl.d2;
-        if (k < 2) {
-            e00 += F[k] * fl.d0;
-            e01 += F[k] * fl.d1;
-            e02 += F[k] * fl.d2;
-        } else {
-            e10 += F[k] * fl.d0;
-            e11 += F[k] * fl.d1;
-            e12 += F[k] * fl.d2;
-        }
-    }
-    e00 *= 2.0; e01 *= 2.0; e02 *= 2.0; e10 *= 2.0; e11 *= 2.0; e12 *= 2.0;
-    A00 += rt * (e00 * e00 + e10 * e10);
-    A11 += rt * (e01 * e01 + e11 * e11);
-    A01 += rt * (e00 * e01 + e10 * e11);
-    A02 += rt * (e00 * e02 + e10 * e12);
-    A12 += rt * (e01 * e02 + e11 * e12);
-    A22 += rt * (e02 * e02 + e12 * e12);
-    const double rwi = vi * vi - sT[4 * S], rti = x[2] - sT[5 * S];
-    const double rwj = vj * vj - sT[6 * S], rtj = x[3] - sT[7 * S];
-    f = 0.5 * rpq * fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
+    EndSums E = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double e00, e01, e02, e10, e11, e12;
+    end_terms(true, gii, -bii, vi, vj, vv, Ti, Tpi, F[0], F[1], sT[0 * S], sT[1 * S], rpq, mu0,
+                    E, e00, e01, e02);
+    end_terms(false, gjj, -bjj, vi, vj, vv, Tj, Tpj, F[2], F[3], sT[2 * S], sT[3 * S], rpq, mu1,
+                     E, e10, e11, e12);
+    // the AL terms' Gauss-Newton part rt grad h grad h'
+    const double r00 = rt * e00, r01 = rt * e01, r02 = rt * e02;
+    const double r10 = rt * e10, r11 = rt * e11, r12 = rt * e12;
+    const double A00 = E.A00 + (r00 * e00 + r10 * e10);
+    const double A11 = E.A11 + (r01 * e01 + r11 * e11);
+    const double A01 = E.A01 + (r00 * e01 + r10 * e11);
+    const double A02 = E.A02 + (r00 * e02 + r10 * e12);
+    const double A12 = E.A12 + (r01 * e02 + r11 * e12);
+    const double A22 = E.A22 + (r02 * e02 + r12 * e12);
+    const double rwi = wi - sT[4 * S], rti = x[2] - sT[5 * S];
+    const double rwj = wj - sT[6 * S], rtj = x[3] - sT[7 * S];
+    f = 0.5 * rpq * E.fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
       + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
-    g[0] = G0 + 2.0 * rva * rwi * vi;
-    g[1] = G1 + 2.0 * rva * rwj * vj;
-    g[2] = G2 + rva * rti;
-    g[3] = -G2 + rva * rtj;
+    g[0] = E.G0 + 2.0 * rva * rwi * vi;
+    g[1] = E.G1 + 2.0 * rva * rwj * vj;
+    g[2] = E.G2 + rva * rti;
+    g[3] = -E.G2 + rva * rtj;
     g[4] = mu0;
     g[5] = mu1;
-    H[P(0, 0)] = A00 + rva * (4.0 * vi * vi + 2.0 * rwi);
+    H[P(0, 0)] = A00 + rva * (4.0 * wi + 2.0 * rwi);
     H[P(0, 1)] = A01;
     H[P(0, 2)] = A02;
     H[P(0, 3)] = -A02;
-    H[P(0, 4)] = rt * e00;
-    H[P(0, 5)] = rt * e10;
-    H[P(1, 1)] = A11 + rva * (4.0 * vj * vj + 2.0 * rwj);
+    H[P(0, 4)] = r00;
+    H[P(0, 5)] = r10;
+    H[P(1, 1)] = A11 + rva * (4.0 * wj + 2.0 * rwj);
     H[P(1, 2)] = A12;
     H[P(1, 3)] = -A12;
-    H[P(1, 4)] = rt * e01;
-    H[P(1, 5)] = rt * e11;
+    H[P(1, 4)] = r01;
+    H[P(1, 5)] = r11;
     H[P(2, 2)] = A22 + rva;
     H[P(2, 3)] = -A22;
-    H[P(2, 4)] = rt * e02;
-    H[P(2, 5)] = rt * e12;
+    H[P(2, 4)] = r02;
+    H[P(2, 5)] = r12;
     H[P(3, 3)] = A22 + rva;
-    H[P(3, 4)] = -rt * e02;
-    H[P(3, 5)] = -rt * e12;
+    H[P(3, 4)] = -r02;
+    H[P(3, 5)] = -r12;
     H[P(4, 4)] = rt;
     H[P(4, 5)] = 0.0;
     H[P(5, 5)] = rt;
@@ -291,61 +271,50 @@ __device__ __forceinline__ void evaluate2(unsigned m, const double *sY, const do
     sincos(x[2] - x[3], &s, &c);
     const double vv = vi * vj;
     constexpr int S = kBranchBlock;
-    const double gii = sY[0 * S], bii = sY[1 * S], gij = sY[2 * S], bij = sY[3 * S];
-    const double gji = sY[4 * S], bji = sY[5 * S], gjj = sY[6 * S], bjj = sY[7 * S];
-    Flow fl[2];
-    flow_end(od, od ? gjj : gii, od ? gji : gij, od ? -bji : bij, vi, vj, vv, c, s, fl[0]);
-    flow_end(od, od ? -bjj : -bii, od ? -bji : -bij, od ? -gji : gij, vi, vj, vv, c, s, fl[1]);
-    const double hm = fl[0].F * fl[0].F + fl[1].F * fl[1].F + (od ? x[5] : x[4]);
+    // my end's p flow (al, be) and self coefficients, as in evaluate1
+    const double al = od ? sY[4 * S] : sY[2 * S];                 // g_ji : g_ij
+    const double be = od ? -sY[5 * S] : sY[3 * S];                // -b_ji : b_ij
+    const double ap = od ? sY[6 * S] : sY[0 * S];                 // g_jj : g_ii
+    const double aq = od ? -sY[7 * S] : -sY[1 * S];               // -b_jj : -b_ii
+    const double T = al * c + be * s, Tp = be * c - al * s;
+    const double wk2 = od ? vj * vj : vi * vi;
+    const double vP = vv * Tp;
+    const double Fp = ap * wk2 + vv * T;
+    const double Fq = aq * wk2 + (od ? vP : -vP);
+    const double hm = Fp * Fp + Fq * Fq + (od ? x[5] : x[4]);
     const double mum = (od ? lt1 : lt0) + rt * hm;
-    double G0 = 0.0, G1 = 0.0, G2 = 0.0, fq = 0.0;
-    double A00 = 0.0, A11 = 0.0, A01 = 0.0, A02 = 0.0, A12 = 0.0, A22 = 0.0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const double r = fl[k].F - sT[(od ? 2 + k : k) * S];
-        fq += r * r;
-        const double ck = rpq * r + 2.0 * mum * fl[k].F;
-        const double wk = rpq + 2.0 * mum;
-        G0 += ck * fl[k].d0;
-        G1 += ck * fl[k].d1;
-        G2 += ck * fl[k].d2;
-        A00 += ck * fl[k].h00 + wk * fl[k].d0 * fl[k].d0;
-        A11 += ck * fl[k].h11 + wk * fl[k].d1 * fl[k].d1;
-        A01 += ck * fl[k].h01 + wk * fl[k].d0 * fl[k].d1;
-        A02 += ck * fl[k].h02 + wk * fl[k].d0 * fl[k].d2;
-        A12 += ck * fl[k].h12 + wk * fl[k].d1 * fl[k].d2;
-        A22 += ck * fl[k].h22 + wk * fl[k].d2 * fl[k].d2;
-    }
-    // gradient of my end's h in (v_i, v_j, th)
-    const double em0 = 2.0 * (fl[0].F * fl[0].d0 + fl[1].F * fl[1].d0);
-    const double em1 = 2.0 * (fl[0].F * fl[0].d1 + fl[1].F * fl[1].d1);
-    const double em2 = 2.0 * (fl[0].F * fl[0].d2 + fl[1].F * fl[1].d2);
+    EndSums E = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double em0, em1, em2;
+    end_terms(!od, ap, aq, vi, vj, vv, T, Tp, Fp, Fq, sT[(od ? 2 : 0) * S], sT[(od ? 3 : 1) * S],
+              rpq, mum, E, em0, em1, em2);
     // swap with the partner; (from, to) in a fixed order on both lanes
-    const double pG0 = partner(m, G0), pG1 = partner(m, G1), pG2 = partner(m, G2);
-    const double pA00 = partner(m, A00), pA11 = partner(m, A11), pA01 = partner(m, A01);
-    const double pA02 = partner(m, A02), pA12 = partner(m, A12), pA22 = partner(m, A22);
-    const double pfq = partner(m, fq), ph = partner(m, hm);
+    const double pG0 = partner(m, E.G0), pG1 = partner(m, E.G1), pG2 = partner(m, E.G2);
+    const double pA00 = partner(m, E.A00), pA11 = partner(m, E.A11), pA01 = partner(m, E.A01);
+    const double pA02 = partner(m, E.A02), pA12 = partner(m, E.A12), pA22 = partner(m, E.A22);
+    const double pfq = partner(m, E.fq), ph = partner(m, hm);
     const double pe0 = partner(m, em0), pe1 = partner(m, em1), pe2 = partner(m, em2);
-    const double pF0 = partner(m, fl[0].F), pF1 = partner(m, fl[1].F);
-    G0 += pG0; G1 += pG1; G2 += pG2;
-    A00 += pA00; A11 += pA11; A01 += pA01; A02 += pA02; A12 += pA12; A22 += pA22;
-    fq += pfq;
+    const double pFp = partner(m, Fp), pFq = partner(m, Fq);
+    const double G0 = E.G0 + pG0, G1 = E.G1 + pG1, G2 = E.G2 + pG2;
+    const double fq = E.fq + pfq;
     const double h0 = od ? ph : hm, h1 = od ? hm : ph;
     const double mu0 = lt0 + rt * h0, mu1 = lt1 + rt * h1;
     const double e00 = od ? pe0 : em0, e01 = od ? pe1 : em1, e02 = od ? pe2 : em2;
     const double e10 = od ? em0 : pe0, e11 = od ? em1 : pe1, e12 = od ? em2 : pe2;
-    F[0] = od ? pF0 : fl[0].F;
-    F[1] = od ? pF1 : fl[1].F;
-    F[2] = od ? fl[0].F : pF0;
-    F[3] = od ? fl[1].F : pF1;
-    A00 += rt * (e00 * e00 + e10 * e10);
-    A11 += rt * (e01 * e01 + e11 * e11);
-    A01 += rt * (e00 * e01 + e10 * e11);
-    A02 += rt * (e00 * e02 + e10 * e12);
-    A12 += rt * (e01 * e02 + e11 * e12);
-    A22 += rt * (e02 * e02 + e12 * e12);
-    const double rwi = vi * vi - sT[4 * S], rti = x[2] - sT[5 * S];
-    const double rwj = vj * vj - sT[6 * S], rtj = x[3] - sT[7 * S];
+    F[0] = od ? pFp : Fp;
+    F[1] = od ? pFq : Fq;
+    F[2] = od ? Fp : pFp;
+    F[3] = od ? Fq : pFq;
+    const double r00 = rt * e00, r01 = rt * e01, r02 = rt * e02;
+    const double r10 = rt * e10, r11 = rt * e11, r12 = rt * e12;
+    const double A00 = (E.A00 + pA00) + (r00 * e00 + r10 * e10);
+    const double A11 = (E.A11 + pA11) + (r01 * e01 + r11 * e11);
+    const double A01 = (E.A01 + pA01) + (r00 * e01 + r10 * e11);
+    const double A02 = (E.A02 + pA02) + (r00 * e02 + r10 * e12);
+    const double A12 = (E.A12 + pA12) + (r01 * e02 + r11 * e12);
+    const double A22 = (E.A22 + pA22) + (r02 * e02 + r12 * e12);
+    const double wi = vi * vi, wj = vj * vj;
+    const double rwi = wi - sT[4 * S], rti = x[2] - sT[5 * S];
+    const double rwj = wj - sT[6 * S], rtj = x[3] - sT[7 * S];
     f = 0.5 * rpq * fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
       + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
     g[0] = G0 + 2.0 * rva * rwi * vi;
@@ -354,24 +323,24 @@ __device__ __forceinline__ void evaluate2(unsigned m, const double *sY, const do
     g[3] = -G2 + rva * rtj;
     g[4] = mu0;
     g[5] = mu1;
-    H[P(0, 0)] = A00 + rva * (4.0 * vi * vi + 2.0 * rwi);
+    H[P(0, 0)] = A00 + rva * (4.0 * wi + 2.0 * rwi);
     H[P(0, 1)] = A01;
     H[P(0, 2)] = A02;
     H[P(0, 3)] = -A02;
-    H[P(0, 4)] = rt * e00;
-    H[P(0, 5)] = rt * e10;
-    H[P(1, 1)] = A11 + rva * (4.0 * vj * vj + 2.0 * rwj);
+    H[P(0, 4)] = r00;
+    H[P(0, 5)] = r10;
+    H[P(1, 1)] = A11 + rva * (4.0 * wj + 2.0 * rwj);
     H[P(1, 2)] = A12;
     H[P(1, 3)] = -A12;
-    H[P(1, 4)] = rt * e01;
-    H[P(1, 5)] = rt * e11;
+    H[P(1, 4)] = r01;
+    H[P(1, 5)] = r11;
     H[P(2, 2)] = A22 + rva;
     H[P(2, 3)] = -A22;
-    H[P(2, 4)] = rt * e02;
-    H[P(2, 5)] = rt * e12;
+    H[P(2, 4)] = r02;
+    H[P(2, 5)] = r12;
     H[P(3, 3)] = A22 + rva;
-    H[P(3, 4)] = -rt * e02;
-    H[P(3, 5)] = -rt * e12;
+    H[P(3, 4)] = -r02;
+    H[P(3, 5)] = -r12;
     H[P(4, 4)] = rt;
     H[P(4, 5)] = 0.0;
     H[P(5, 5)] = rt;

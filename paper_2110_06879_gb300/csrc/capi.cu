@@ -573,7 +573,8 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     for (int s = 0; s < S; ++s)
         for (int k = h->slot_off[s]; k < h->slot_off[s + 1]; ++k) slot_scen[k] = s;
     {
-        // branch_tron is persistent: at most kBranchBlocksPerSM blocks per SM
+        // branch_tron is persistent: its blocks pull branches from a queue and
+        // none waits on another, so any block count is correct
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
@@ -581,7 +582,9 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
         cudaGetLastError();
         h->lanes = op.lanes_per_branch == 2 ? 2 : 1;
         const int need = branch_blocks_needed(nl, h->lanes);
-        const int cap = op.branch_blocks > 0 ? op.branch_blocks : sms * kBranchBlocksPerSM;
+        // default: two blocks per SM (two warps per sub-partition hide part of
+        // the FP64 latency) when the branches fill every slot of them, else one
+        const int cap = op.branch_blocks > 0 ? op.branch_blocks : (need >= 2 * sms ? 2 * sms : sms);
         h->nblk_branch = need < cap ? need : cap;
     }
     h->nblk_bus = h->blk_off[S];
