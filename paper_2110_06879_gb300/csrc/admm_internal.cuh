@@ -133,8 +133,8 @@ constexpr int kBranchBlock = 128;
 constexpr int kBranchBlocksPerSM = 1;   // launch bound: 255 registers a lane (two blocks still fit an SM)
 // dynamic shared memory of a branch_tron block: per lane, the branch data
 // (Y[8], t[8]), the packed Hessian, the preconditioner's packed factor and the
-// scaled matrix it factors (21 doubles each)
-constexpr size_t kBranchSmem = (size_t)(16 + 3 * 21) * kBranchBlock * sizeof(double);
+// scaled matrix it factors (21 doubles each), and the scaling (6)
+constexpr size_t kBranchSmem = (size_t)(16 + 3 * 21 + 6) * kBranchBlock * sizeof(double);
 constexpr int kBusBlock = 256;      // threads of a bus_dual block
 constexpr int kBusPerBlock = 256;   // at most this many buses per bus_dual block
 constexpr int kSlotCap = 768;       // at most this many incidence slots per bus_dual block

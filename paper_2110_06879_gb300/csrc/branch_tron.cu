@@ -581,15 +581,14 @@ __device__ __forceinline__ double shift_at(int k, bool pos)
 // is found by bisection over the schedule's indices (about 5 factorisations
 // instead of up to 20 in sequence): A + sigma I stays positive definite as
 // sigma grows, so success is monotone in the index and bisection finds the
-// same shift as trying the shifts in order.  S holds the scaled matrix.
-__device__ __forceinline__ void precond_factor(bool on, SMat H, SMat S, const bool *fr, SMat L,
-                                               double *dinv)
+// same shift as trying the shifts in order.  S holds the scaled matrix, Dv the
+// diagonal of D^-1 (lanes with a scaled factor only).  The scaled path is rare
+// and kept out of line, so that the code of the common path stays small.
+__device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned frm, SMat L, SMat Dv)
 {
+    bool fr[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dinv[i] = 1.0;
-    const bool plain = chol_pass<true>(H, fr, 0.0, true, L);
-    const bool need = on && !plain;
-    if (!__any_sync(kFull, need)) return;
+    for (int i = 0; i < 6; ++i) fr[i] = (frm >> i) & 1u;
     bool pos = true;
     double ds[6];
 #pragma unroll
@@ -600,7 +599,7 @@ __device__ __forceinline__ void precond_factor(bool on, SMat H, SMat S, const bo
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        dinv[i] = need ? ds[i] : dinv[i];
+        if (need) Dv[i] = ds[i];
 #pragma unroll
         for (int j = i; j < 6; ++j)
             if (need) S[P(i, j)] = H[P(i, j)] * ds[i] * ds[j];
@@ -632,12 +631,30 @@ __device__ __forceinline__ void precond_factor(bool on, SMat H, SMat S, const bo
     }
 }
 
-__device__ __forceinline__ void precond_solve(SMat L, const double *dinv, const double *r, double *z)
+// Returns whether the lane's factor is the scaled one (warp-collective).
+__device__ __forceinline__ bool precond_factor(bool on, SMat H, SMat S, const bool *fr, SMat L,
+                                               SMat Dv)
+{
+    const bool plain = chol_pass<true>(H, fr, 0.0, true, L);
+    const bool need = on && !plain;
+    if (!__any_sync(kFull, need)) return false;
+    unsigned frm = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) frm |= fr[i] ? 1u << i : 0u;
+    precond_scaled(need, H, S, frm, L, Dv);
+    return need;
+}
+
+// z = M^-1 r, M = D L L' D (D = I unless `scaled`); anys: some lane of the
+// warp has a scaled factor (multiplying by 1 leaves the others' values as
+// they are)
+__device__ __forceinline__ void precond_solve(SMat L, SMat Dv, bool scaled, bool anys, const double *r,
+                                              double *z)
 {
     double t[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double v = r[i] * dinv[i];
+        double v = anys ? r[i] * (scaled ? Dv[i] : 1.0) : r[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) v -= L[P(i, k)] * t[k];
         t[i] = v * L[P(i, i)];
@@ -650,7 +667,7 @@ __device__ __forceinline__ void precond_solve(SMat L, const double *dinv, const 
         t[i] = v * L[P(i, i)];
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) z[i] = t[i] * dinv[i];
+    for (int i = 0; i < 6; ++i) z[i] = anys ? t[i] * (scaled ? Dv[i] : 1.0) : t[i];
 }
 
 // Subspace step: Steihaug PCG on the free variables of the Cauchy point, then
@@ -678,8 +695,9 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     hmul<kL>(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
-    double dinv[6];
-    precond_factor(act, H, S, fr, L, dinv);
+    const SMat Dv{S.p + 21 * kBranchBlock};
+    const bool scaled = precond_factor(act, H, S, fr, L, Dv);
+    const bool anys = __any_sync(kFull, scaled);
     // hwb: H times the boundary step tau p, which CG adds to w without
     // updating r; elsewhere H w = r0 - r on the free variables (r0 = -gc)
     double w[6], r[6], z[6], pv[6], q[6], hwb[6];
@@ -693,7 +711,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     }
     const bool cgon = act && dpos(rn0);
     if (!__any_sync(kFull, cgon)) return;
-    precond_solve(L, dinv, r, z);
+    precond_solve(L, Dv, scaled, anys, r, z);
     double rz = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -742,7 +760,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         }
         go = go && !dle(rn, tol2);
         if (!__any_sync(kFull, go)) break;
-        precond_solve(L, dinv, r, z);
+        precond_solve(L, Dv, scaled, anys, r, z);
         double rz1 = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -851,7 +869,7 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
     const SMat H{sh + 16 * kBranchBlock + threadIdx.x};
     const SMat Lf{sh + 37 * kBranchBlock + threadIdx.x};
-    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};
+    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};   // then D^-1's diagonal (6)
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
