@@ -438,6 +438,27 @@ __device__ __forceinline__ double pgnorm(const Bounds &B, const double *x, const
 }
 
 
+// A Cauchy trial past a breakpoint of the projected path (rare): the projected
+// step t = P(x - a g) - x and its q(t), |t|^2 and g't, kept out of line so
+// that the code of the common path stays small.  Warp-collective for kL = 2.
+struct V6 {
+    double v[6];
+};
+struct Q3 {
+    double q, tt, gt;
+};
+template <int kL>
+__device__ __noinline__ Q3 cauchy_full(const Bounds B, const V6 x, const V6 g, double a, SMat H)
+{
+    double t[6];
+    pstep(B, x.v, g.v, a, t);
+    Q3 r;
+    r.q = qmodel<kL>(g.v, H, t);
+    r.tt = dot6<kL>(t, t);
+    r.gt = dot6<kL>(g.v, t);
+    return r;
+}
+
 // The loops below (Cauchy trials, Cholesky retries, CG, projected search)
 // have data-dependent trip counts.  They are written warp-uniform: every lane
 // of the warp runs every trip, exits are decided with __any_sync, and lanes
@@ -481,13 +502,14 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         q = gs + 0.5 * a * a * GHG;
         bool ok = dle(a * a * G2, d2) && dle(q, kMu0 * gs);
         if (__any_sync(kFull, need && !unc)) {
-            double t[6];
-            pstep(B, x, g, a, t);
             // every lane forms every product (no short-circuit): with two
             // lanes per branch the products exchange values within the pair
-            const double qf = qmodel<kL>(g, H, t);
-            const double tt = dot6<kL>(t, t), gt = dot6<kL>(g, t);
-            const bool okf = dle(tt, d2) && dle(qf, kMu0 * gt);
+            V6 xv, gv;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { xv.v[i] = x[i]; gv.v[i] = g[i]; }
+            const Q3 r = cauchy_full<kL>(B, xv, gv, a, H);
+            const double qf = r.q;
+            const bool okf = dle(r.tt, d2) && dle(qf, kMu0 * r.gt);
             ok = unc ? ok : okf;
             q = unc ? q : qf;
         }
