@@ -80,6 +80,16 @@ __device__ __forceinline__ double amax(double m, double a)
     return ba > __double_as_longlong(m) ? __longlong_as_double(ba) : m;
 }
 
+// v * 2^-k for k >= 0 by an exponent shift on the integer pipe: exact for
+// a normal v whose exponent stays normal; 0 where the result would be
+// subnormal (and for v = 0)
+__device__ __forceinline__ double pow2_scale(double v, int k)
+{
+    const long long b = __double_as_longlong(v);
+    const long long e = (b >> 52) & 0x7ff;
+    return e > k ? __longlong_as_double(b - ((long long)k << 52)) : 0.0;
+}
+
 // Two lanes per branch (kL = 2): lanes 2k and 2k+1 hold the same branch and
 // the same state, bit for bit; the parts of a trip that split cleanly (the two
 // line ends' flows, rows of 6x6 products, halves of 6-vector dot products)
@@ -422,6 +432,28 @@ __device__ __forceinline__ double qmodel(const double *g, SMat H, const double *
     }
 }
 
+// v'Hv / 2 (one lane: from the packed triangle, 33 operations against 42 for
+// H v and a dot product; two lanes: from H v by rows)
+template <int kL = 1>
+__device__ __forceinline__ double half_quad(SMat H, const double *v, unsigned m = kFull)
+{
+    if constexpr (kL == 1) {
+        double q = 0.0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            double t = 0.5 * H[P(i, i)] * v[i];
+#pragma unroll
+            for (int j = i + 1; j < 6; ++j) t += H[P(i, j)] * v[j];
+            q += v[i] * t;
+        }
+        return q;
+    } else {
+        double hv[6];
+        hmul<2>(H, v, hv, m);
+        return 0.5 * dot6<2>(v, hv, m);
+    }
+}
+
 __device__ __forceinline__ void pstep(const Bounds &B, const double *x, const double *g, double a,
                                       double *s)
 {
@@ -486,21 +518,24 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
     for (int i = 0; i < 6; ++i) {
         const bool gp_pos = dpos(g[i]);
         path[i] = (gp_pos && B.above_lo(i, x[i])) || (dneg(g[i]) && B.below_hi(i, x[i]));
-        room[i] = gp_pos ? x[i] - B.lo(i) : B.hi(i) - x[i];
+        room[i] = (gp_pos ? x[i] : B.hi(i)) - (gp_pos ? B.lo(i) : x[i]);
         gp[i] = path[i] ? g[i] : 0.0;
     }
-    double hg[6];
-    hmul<kL>(H, gp, hg);
-    const double G2 = dot6<kL>(gp, gp), GHG = dot6<kL>(gp, hg);
+    const double G2 = dot6<kL>(gp, gp), hGHG = half_quad<kL>(H, gp);   // |g_P|^2, g_P' H g_P / 2
     // sufficient decrease and radius test at alpha = a (uniform across the
-    // warp), with q(s(a)) in q
-    auto ok_at = [&](double a, bool need, double &q) -> bool {
+    // warp), with q(s(a)) in q; `past`: a is past every breakpoint of the path
+    auto ok_at = [&](double a, bool need, double &q, bool &past) -> bool {
         bool unc = true;
+        past = true;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) unc = unc && (!path[i] || dle(a * dabsi(g[i]), room[i]));
-        const double gs = -a * G2;
-        q = gs + 0.5 * a * a * GHG;
-        bool ok = dle(a * a * G2, d2) && dle(q, kMu0 * gs);
+        for (int i = 0; i < 6; ++i) {
+            const double ag = a * dabsi(g[i]);
+            unc = unc && (!path[i] || dle(ag, room[i]));
+            past = past && (!path[i] || dle(room[i], ag));
+        }
+        const double gs = -a * G2, a2 = a * a;
+        q = gs + a2 * hGHG;
+        bool ok = dle(a2 * G2, d2) && dle(q, kMu0 * gs);
         if (__any_sync(kFull, need && !unc)) {
             // every lane forms every product (no short-circuit): with two
             // lanes per branch the products exchange values within the pair
@@ -516,25 +551,23 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         return ok;
     };
     double a = alpha, qa = 0.0;
+    bool pa;                           // a is past every breakpoint
     if (on) c.cauchy++;
-    const bool back = !ok_at(a, on, qa);
+    const bool back = !ok_at(a, on, qa, pa);
     bool go = on;
     for (int t = 0; t < kCauchyTrials; ++t) {
-        if (go && !back) {
-            // the path stops moving once a is past every breakpoint
-            bool past = true;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) past = past && (!path[i] || dle(room[i], a * dabsi(g[i])));
-            go = !past;
-        }
+        // the path stops moving once a is past every breakpoint
+        if (go && !back) go = !pa;
         if (!__any_sync(kFull, go)) break;
         const double an = back ? a * 0.1 : a * 10.0;
         if (go) c.cauchy++;
         double qn;
-        const bool ok = ok_at(an, go, qn);
+        bool pn;
+        const bool ok = ok_at(an, go, qn, pn);
         if (go && (back || ok)) {
             a = an;
             qa = qn;
+            pa = pn;
         }
         if (ok == back) go = false;    // backtracking found a point / extrapolation failed
     }
@@ -812,11 +845,13 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     for (int t = 0; t < kPsTrials; ++t) {
         if (!__any_sync(kFull, ps)) break;
         if (ps) c.ps++;
+        // beta = 2^-t: beta |w_i|, beta gw and beta^2 whw / 2 are exact
+        // exponent shifts, done on the integer pipe
         bool unc = true;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) unc = unc && (!fr[i] || dle(beta * dabsi(w[i]), room[i]));
-        const double bgw = beta * gw;
-        double qb = qc + bgw + 0.5 * beta * beta * whw;
+        for (int i = 0; i < 6; ++i) unc = unc && (!fr[i] || dle(pow2_scale(dabsi(w[i]), t), room[i]));
+        const double bgw = pow2_scale(gw, t);
+        double qb = (qc + bgw) + pow2_scale(whw, 2 * t + 1);
         bool okp = ps && dle(qb, qc + kMu0 * bgw);
         const bool full = __any_sync(kFull, ps && !unc);
         if (full || __any_sync(kFull, okp)) {
