@@ -830,12 +830,16 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     // Projected search along w from the Cauchy point.  While xc + beta w
     // stays inside the bounds (beta below every free variable's
     // breakpoint), q(sc + beta w) = q(sc) + beta gc'w + beta^2/2 w'Hw in
-    // closed form, with H w from the CG recurrences; trials past a
-    // breakpoint evaluate the projection in full.
+    // closed form, with H w from the CG recurrences.  Past a breakpoint the
+    // projected step is sc + beta w + e, e_i = bound_i - (xc_i + beta w_i) on
+    // the variables past theirs, and q = q(sc + beta w) + gc'e + beta (Hw)'e
+    // + e'He/2, formed over those variables only.  S (free once the factor is
+    // made) keeps H w in S[0..5] and e in S[6..11].
     double gw = 0.0, whw = 0.0, room[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const double hw = fr[i] ? (-gc[i] - r[i]) + hwb[i] : 0.0;
+        S[i] = hw;
         gw += gc[i] * w[i];
         whw += w[i] * hw;
         room[i] = dpos(w[i]) ? B.hi(i) - xc[i] : xc[i] - B.lo(i);
@@ -853,23 +857,33 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         const double bgw = pow2_scale(gw, t);
         double qb = (qc + bgw) + pow2_scale(whw, 2 * t + 1);
         bool okp = ps && dle(qb, qc + kMu0 * bgw);
-        const bool full = __any_sync(kFull, ps && !unc);
-        if (full || __any_sync(kFull, okp)) {
-            double sb[6];
+        if (__any_sync(kFull, ps && !unc)) {
+            double ge = 0.0, he = 0.0, ehe = 0.0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) sb[i] = B.clamp(i, xc[i] + beta * w[i]) - x[i];
-            if (full) {
-                double dd[6];
+            for (int i = 0; i < 6; ++i) S[6 + i] = 0.0;
 #pragma unroll
-                for (int i = 0; i < 6; ++i) dd[i] = sb[i] - sc[i];
-                const double qf = qmodel<kL>(g, H, sb);
-                const double gdd = dot6<kL>(gc, dd);          // on every lane (see cauchy)
-                const bool okf = ps && dle(qf, qc + kMu0 * gdd);
-                qb = unc ? qb : qf;
-                okp = unc ? okp : okf;
+            for (int i = 0; i < 6; ++i) {
+                const double bwi = pow2_scale(dabsi(w[i]), t);
+                const bool cl = fr[i] && !dle(bwi, room[i]);
+                if (__any_sync(kFull, cl)) {
+                    const double ei = cl ? (dpos(w[i]) ? room[i] - bwi : bwi - room[i]) : 0.0;
+                    ge += gc[i] * ei;
+                    he += S[i] * ei;
+                    double th = 0.5 * H[P(i, i)] * ei;
+#pragma unroll
+                    for (int j = 0; j < i; ++j) th += H[P(i, j)] * S[6 + j];
+                    ehe += ei * th;
+                    S[6 + i] = ei;
+                }
             }
+            const double qf = qb + (ge + pow2_scale(he, t)) + ehe;
+            const bool okf = ps && dle(qf, qc + kMu0 * (bgw + ge));
+            qb = unc ? qb : qf;
+            okp = unc ? okp : okf;
+        }
+        if (__any_sync(kFull, okp)) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) s[i] = okp ? sb[i] : s[i];
+            for (int i = 0; i < 6; ++i) s[i] = okp ? B.clamp(i, xc[i] + beta * w[i]) - x[i] : s[i];
         }
         qs = okp ? qb : qs;
         ps = ps && !okp;
