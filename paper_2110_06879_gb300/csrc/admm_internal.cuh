@@ -132,9 +132,10 @@ __global__ void finalize_kernel(DevGrid G, Range R, double *pg, double *qg, doub
 constexpr int kBranchBlock = 128;
 constexpr int kBranchBlocksPerSM = 1;   // launch bound: 255 registers a lane (two blocks still fit an SM)
 // dynamic shared memory of a branch_tron block: per lane, the branch data
-// (Y[8], t[8]), the packed Hessian, the preconditioner's packed factor and the
-// scaled matrix it factors (21 doubles each), and the scaling (6)
-constexpr size_t kBranchSmem = (size_t)(16 + 3 * 21 + 6) * kBranchBlock * sizeof(double);
+// (Y[8], t[8]), the packed Hessian and the preconditioner's packed factor (21
+// doubles each) and a scratch of 12 (the preconditioner's scaling during CG,
+// H w and the clamped part of a projected step in the search)
+constexpr size_t kBranchSmem = (size_t)(16 + 2 * 21 + 12) * kBranchBlock * sizeof(double);
 constexpr int kBusBlock = 256;      // threads of a bus_dual block
 constexpr int kBusPerBlock = 256;   // at most this many buses per bus_dual block
 constexpr int kSlotCap = 768;       // at most this many incidence slots per bus_dual block

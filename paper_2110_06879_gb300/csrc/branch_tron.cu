@@ -587,17 +587,24 @@ __device__ __forceinline__ double boundary_tau(const double *a, const double *pv
 }
 
 // One Cholesky pass of M + sigma I on the free block (identity on fixed
-// variables), M = H (kPlain, sigma = 0) or the scaled matrix D^-1 H D^-1; the
-// diagonal of the factor keeps the reciprocal pivots.  The pass runs in
-// registers; lanes with write == true store the factor to L.
+// variables), M = H (kPlain, sigma = 0) or the scaled matrix D^-1 H D^-1
+// (ds = diag(D^-1)); the diagonal of the factor keeps the reciprocal pivots.
+// The pass runs in registers; lanes with write == true store the factor to L.
 template <bool kPlain>
-__device__ __forceinline__ bool chol_pass(SMat M, const bool *fr, double sigma, bool write, SMat L)
+__device__ __forceinline__ double scaled_entry(SMat H, const double *ds, int i, int j)
+{
+    return kPlain ? H[P(i, j)] : H[P(i, j)] * ds[i] * ds[j];
+}
+
+template <bool kPlain>
+__device__ __forceinline__ bool chol_pass(SMat H, const double *ds, const bool *fr, double sigma,
+                                          bool write, SMat L)
 {
     double l[21];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
-        double dd = fr[j] ? (kPlain ? M[P(j, j)] : M[P(j, j)] + sigma) : 1.0;
+        double dd = fr[j] ? (kPlain ? H[P(j, j)] : scaled_entry<false>(H, ds, j, j) + sigma) : 1.0;
 #pragma unroll
         for (int k = 0; k < j; ++k) dd -= l[P(j, k)] * l[P(j, k)];
         ok = ok && dpos(dd);
@@ -605,7 +612,7 @@ __device__ __forceinline__ bool chol_pass(SMat M, const bool *fr, double sigma, 
         l[P(j, j)] = linv;
 #pragma unroll
         for (int i = j + 1; i < 6; ++i) {
-            double v = (fr[i] && fr[j]) ? M[P(i, j)] : 0.0;
+            double v = (fr[i] && fr[j]) ? scaled_entry<kPlain>(H, ds, i, j) : 0.0;
 #pragma unroll
             for (int k = 0; k < j; ++k) v -= l[P(i, k)] * l[P(j, k)];
             l[P(i, j)] = v * linv;
@@ -636,10 +643,10 @@ __device__ __forceinline__ double shift_at(int k, bool pos)
 // is found by bisection over the schedule's indices (about 5 factorisations
 // instead of up to 20 in sequence): A + sigma I stays positive definite as
 // sigma grows, so success is monotone in the index and bisection finds the
-// same shift as trying the shifts in order.  S holds the scaled matrix, Dv the
-// diagonal of D^-1 (lanes with a scaled factor only).  The scaled path is rare
-// and kept out of line, so that the code of the common path stays small.
-__device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned frm, SMat L, SMat Dv)
+// same shift as trying the shifts in order.  Dv receives the diagonal of D^-1
+// (lanes with a scaled factor only).  The scaled path is rare and kept out of
+// line, so that the code of the common path stays small.
+__device__ __noinline__ void precond_scaled(bool need, SMat H, unsigned frm, SMat L, SMat Dv)
 {
     bool fr[6];
 #pragma unroll
@@ -653,12 +660,8 @@ __device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned 
         pos = pos && (!fr[i] || dpos(a));
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 6; ++i)
         if (need) Dv[i] = ds[i];
-#pragma unroll
-        for (int j = i; j < 6; ++j)
-            if (need) S[P(i, j)] = H[P(i, j)] * ds[i] * ds[j];
-    }
     // first success in [lo, hi]; hi == kCholTries: none found yet.  `held`:
     // L holds the factor at hi (the lane's last pass succeeded)
     int lo = 0, hi = kCholTries;
@@ -666,7 +669,7 @@ __device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned 
     for (int t = 0; t < 8; ++t) {
         if (!__any_sync(kFull, srch)) break;
         const int mid = (lo + hi) >> 1;
-        const bool ok = chol_pass<false>(S, fr, shift_at(mid, pos), srch, L);
+        const bool ok = chol_pass<false>(H, ds, fr, shift_at(mid, pos), srch, L);
         if (srch) {
             hi = ok ? mid : hi;
             lo = ok ? lo : mid + 1;
@@ -675,7 +678,7 @@ __device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned 
         srch = srch && lo < hi;
     }
     const bool redo = need && hi < kCholTries && !held;
-    if (__any_sync(kFull, redo)) chol_pass<false>(S, fr, shift_at(hi, pos), redo, L);
+    if (__any_sync(kFull, redo)) chol_pass<false>(H, ds, fr, shift_at(hi, pos), redo, L);
     if (__any_sync(kFull, need && hi >= kCholTries)) {   // give up: identity in the scaled space
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -687,16 +690,15 @@ __device__ __noinline__ void precond_scaled(bool need, SMat H, SMat S, unsigned 
 }
 
 // Returns whether the lane's factor is the scaled one (warp-collective).
-__device__ __forceinline__ bool precond_factor(bool on, SMat H, SMat S, const bool *fr, SMat L,
-                                               SMat Dv)
+__device__ __forceinline__ bool precond_factor(bool on, SMat H, const bool *fr, SMat L, SMat Dv)
 {
-    const bool plain = chol_pass<true>(H, fr, 0.0, true, L);
+    const bool plain = chol_pass<true>(H, nullptr, fr, 0.0, true, L);
     const bool need = on && !plain;
     if (!__any_sync(kFull, need)) return false;
     unsigned frm = 0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) frm |= fr[i] ? 1u << i : 0u;
-    precond_scaled(need, H, S, frm, L, Dv);
+    precond_scaled(need, H, frm, L, Dv);
     return need;
 }
 
@@ -750,8 +752,8 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     hmul<kL>(H, sc, gc);
 #pragma unroll
     for (int i = 0; i < 6; ++i) gc[i] += g[i];
-    const SMat Dv{S.p + 21 * kBranchBlock};
-    const bool scaled = precond_factor(act, H, S, fr, L, Dv);
+    const SMat Dv = S;                     // the scratch holds D^-1 until CG ends
+    const bool scaled = precond_factor(act, H, fr, L, Dv);
     const bool anys = __any_sync(kFull, scaled);
     // hwb: H times the boundary step tau p, which CG adds to w without
     // updating r; elsewhere H w = r0 - r on the free variables (r0 = -gc)
@@ -833,8 +835,8 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
     // closed form, with H w from the CG recurrences.  Past a breakpoint the
     // projected step is sc + beta w + e, e_i = bound_i - (xc_i + beta w_i) on
     // the variables past theirs, and q = q(sc + beta w) + gc'e + beta (Hw)'e
-    // + e'He/2, formed over those variables only.  S (free once the factor is
-    // made) keeps H w in S[0..5] and e in S[6..11].
+    // + e'He/2, formed over those variables only.  The scratch S (free once
+    // CG is done) keeps H w in S[0..5] and e in S[6..11].
     double gw = 0.0, whw = 0.0, room[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -935,12 +937,12 @@ template <int kL>
 __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
 {
     // dynamic shared memory, per lane with stride kBranchBlock: Y[8], t[8],
-    // then the packed Hessian, the preconditioner's factor and scaled matrix
+    // then the packed Hessian, the preconditioner's factor and a scratch of 12
     extern __shared__ double sh[];
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
     const SMat H{sh + 16 * kBranchBlock + threadIdx.x};
     const SMat Lf{sh + 37 * kBranchBlock + threadIdx.x};
-    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};   // then D^-1's diagonal (6)
+    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
