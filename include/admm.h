@@ -87,7 +87,7 @@ typedef struct {
     double tol_in_decay;   /*   tol_in_decay^k)  (1e-2, 0.5)                         */
     double al_rho0;        /* initial rho-tilde of a branch solve; <= 0: 25 rho_pq / rbar^2,
                               rbar the tightened rating (rho_pq without a limit)  */
-    double al_tol;         /* line-limit AL stops when max|h| <= al_tol (1e-8)       */
+    double al_tol;         /* line-limit AL stops when max|h| <= al_tol (1e-6)       */
     double al_decay;       /* rho-tilde grows unless max|h| fell below this share (0.1)  */
     double al_rho_factor;  /* rho-tilde growth (100)                                 */
     double al_rho_max;     /* cap on rho-tilde (1e12)                                */

@@ -72,7 +72,7 @@ def default_options(**kw) -> dict:
     parameters the paper leaves open."""
     o = dict(rho_pq=10.0, rho_va=1000.0, obj_scale=1.0, line_limit_frac=0.99,
              beta0=0.0, beta_factor=6.0, z_decay=0.8, beta_max=1e12, lambda_max=1e12,
-             tol_in0=1e-2, tol_in_decay=0.5, al_rho0=0.0, al_tol=1e-8, al_decay=0.1,
+             tol_in0=1e-2, tol_in_decay=0.5, al_rho0=0.0, al_tol=1e-6, al_decay=0.1,
              al_rho_factor=100.0, al_rho_max=1e12, tron_gtol=1e-10, tron_ftol=1e-12, tron_xtol=1e-13,
              two_level=1, max_outer=20, max_inner=1000, al_max_iter=20, tron_max_iter=200,
              beta_rule=0)

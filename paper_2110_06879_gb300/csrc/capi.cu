@@ -99,7 +99,7 @@ extern "C" void admm_default_options(admm_options *o)
     o->tol_in0 = 1e-2;
     o->tol_in_decay = 0.5;
     o->al_rho0 = 0.0;
-    o->al_tol = 1e-8;
+    o->al_tol = 1e-6;
     o->al_decay = 0.1;
     o->al_rho_factor = 100.0;
     o->al_rho_max = 1e12;

@@ -535,7 +535,9 @@ def test_branch_al_loop_solves_line_limited_problem(oracle_mod, binding):
     two perturbed starts, each point refined by Newton on its KKT system; the
     best such point must be the loop's (1e-7), with the same Lagrangian value
     (the loop stops at |h| <= al_tol, so compare f0 + sum lt h) to 1e-10
-    relative and the same multipliers to 1e-5 relative."""
+    relative and the same multipliers to 1e-5 relative.  The loop runs at
+    al_tol = 1e-8 for these checks; at the default 1e-6 it must stop with
+    |h| <= 1e-6 within 1e-5 of that point."""
     from scipy.optimize import minimize
     rng = np.random.default_rng(31 if binding else 37)
     n_active = 0
@@ -543,7 +545,16 @@ def test_branch_al_loop_solves_line_limited_problem(oracle_mod, binding):
         bp, x0, _ = _random_prob(oracle_mod, rng, lt=np.zeros(2), rate=0.3 if binding else None)
         lo, hi = np.array(bp.lo[:]), np.array(bp.hi[:])
         rbar2 = -lo[4]
-        x, lt, rt, st = oracle_mod.branch_solve(bp, x0)
+        bpd = type(bp).from_buffer_copy(bp)    # the loop mutates lt and rt
+        # the loop at a tight stopping tolerance, so that its multipliers are
+        # accurate enough for the KKT checks below
+        x, lt, rt, st = oracle_mod.branch_solve(bp, x0, al_tol=1e-8)
+        # at the default tolerance (1e-6) the loop stops on its own test, near
+        # the tight solution
+        xd, _, _, _ = oracle_mod.branch_solve(bpd, x0)
+        hd = np.array(_branch_parts_analytic(bpd, xd[:4])[1]) + xd[4:]
+        assert np.abs(hd).max() <= 1e-6, (it, hd)
+        assert np.abs(xd[:4] - x[:4]).max() <= 1e-5, (it, xd, x)
         v = x[:4]
         f0, pq = _branch_parts_analytic(bp, v)
         # (1) feasibility: h = p^2 + q^2 + s vanishes to al_tol, slack in bounds
