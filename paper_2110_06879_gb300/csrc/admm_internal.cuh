@@ -66,6 +66,8 @@ struct DevOpts {
     double al_rho0, al_tol, al_decay, al_rho_factor, al_rho_max;
     double tron_gtol, tron_ftol, tron_xtol;
     int32_t two_level, max_outer, max_inner, al_max_iter, tron_max_iter, beta_rule;
+    int32_t num_sms;               // SMs of the device (branch_tron's trip barrier)
+    int32_t pad_;
 };
 
 struct DevGrid {

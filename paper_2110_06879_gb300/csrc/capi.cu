@@ -75,6 +75,7 @@ struct admm_handle {
     int32_t sel = 0;             // scenario addressed by the per-scenario calls
     int nblk_branch = 0, nblk_bus = 0, nblk_fin = 0, nblk_flush = 0;
     int lanes = 1;               // lanes per branch of branch_tron (1 or 2)
+    int sms = 152;               // SMs of the device
     // iteration graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -580,6 +581,7 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 152;
         cudaGetLastError();
+        h->sms = sms;
         h->lanes = op.lanes_per_branch == 2 ? 2 : 1;
         const int need = branch_blocks_needed(nl, h->lanes);
         // default: two blocks per SM (two warps per sub-partition hide part of
@@ -649,6 +651,8 @@ extern "C" int admm_create_batch(const admm_grid *grids, int32_t nscen, const ad
     O.two_level = op.two_level; O.max_outer = op.max_outer; O.max_inner = op.max_inner;
     O.al_max_iter = op.al_max_iter; O.tron_max_iter = op.tron_max_iter;
     O.beta_rule = op.beta_rule;
+    O.num_sms = h->sms;
+    O.pad_ = 0;
     // uploads (host staging in the device layout)
     {
         std::vector<double> bus(6 * (size_t)nb), raw(6 * (size_t)nl), gc(3 * (size_t)ng + 1),
