@@ -791,7 +791,7 @@ def main():
     ap.add_argument("--sizes", type=int, nargs="*", default=[2000, 10000],
                     help="smaller grids timed to 1e-3 and to the violation target")
     ap.add_argument("--size-rho", type=float, nargs=2, default=[3e3, 3e4])
-    ap.add_argument("--gap-max-nbus", type=int, default=2000,
+    ap.add_argument("--gap-max-nbus", type=int, default=10000,
                     help="largest grid whose objective is compared with an oracle solve")
     ap.add_argument("--lanes-nbus", type=int, default=10000,
                     help="grid of --sizes on which one and two lanes per branch are compared")
