@@ -135,9 +135,10 @@ constexpr int kBranchBlock = 128;
 constexpr int kBranchBlocksPerSM = 1;   // launch bound: 255 registers a lane (two blocks still fit an SM)
 // dynamic shared memory of a branch_tron block: per lane, the branch data
 // (Y[8], t[8]), the packed Hessian and the preconditioner's packed factor (21
-// doubles each) and a scratch of 12 (the preconditioner's scaling during CG,
-// H w and the clamped part of a projected step in the search)
-constexpr size_t kBranchSmem = (size_t)(16 + 2 * 21 + 12) * kBranchBlock * sizeof(double);
+// doubles each, stored in 11 pairs) and a scratch of 12 (the preconditioner's
+// scaling during CG, H w and the clamped part of a projected step in the
+// search)
+constexpr size_t kBranchSmem = (size_t)(16 + 2 * 22 + 12) * kBranchBlock * sizeof(double);
 constexpr int kBusBlock = 256;      // threads of a bus_dual block
 constexpr int kBusPerBlock = 256;   // at most this many buses per bus_dual block
 constexpr int kSlotCap = 768;       // at most this many incidence slots per bus_dual block

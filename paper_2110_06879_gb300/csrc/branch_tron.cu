@@ -40,13 +40,18 @@ __host__ __device__ constexpr int P(int i, int j)
     return i <= j ? (i * (11 - i)) / 2 + j : (j * (11 - j)) / 2 + i;
 }
 
-// A lane's packed symmetric matrices (the Hessian, the preconditioner's
-// factor and the scaled matrix it factors) live in shared memory, the block's
-// lanes interleaved (stride kBranchBlock): held in registers each costs 42 of
-// the 255 a lane has, and the subspace step then spills.
+// A lane's packed symmetric matrices (the Hessian and the preconditioner's
+// factor) and its scratch live in shared memory: held in registers each
+// matrix costs 42 of the 255 registers a lane has, and the subspace step then
+// spills.  Entries are stored in pairs, the block's lanes interleaved pair by
+// pair (entry k of lane t at (k / 2) * 2 kBranchBlock + 2 t + k % 2), so that
+// two consecutive entries are one 16-byte access.
 struct SMat {
-    double *p;
-    __device__ __forceinline__ double &operator[](int k) const { return p[k * kBranchBlock]; }
+    double *p;   // the lane's first pair
+    __device__ __forceinline__ double &operator[](int k) const
+    {
+        return p[(k >> 1) * (2 * kBranchBlock) + (k & 1)];
+    }
 };
 
 struct Cnt {
@@ -936,13 +941,14 @@ enum LaneState { LS_IDLE = 0, LS_INIT = 1, LS_ITER = 2, LS_REEVAL = 3, LS_DONE =
 template <int kL>
 __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
 {
-    // dynamic shared memory, per lane with stride kBranchBlock: Y[8], t[8],
+    // dynamic shared memory: Y[8], t[8] per lane with stride kBranchBlock,
     // then the packed Hessian, the preconditioner's factor and a scratch of 12
+    // in pairs (SMat)
     extern __shared__ double sh[];
     __shared__ unsigned cstart[kClasses + 1];  // queue positions where the classes start
-    const SMat H{sh + 16 * kBranchBlock + threadIdx.x};
-    const SMat Lf{sh + 37 * kBranchBlock + threadIdx.x};
-    const SMat Sc{sh + 58 * kBranchBlock + threadIdx.x};
+    const SMat H{sh + 16 * kBranchBlock + 2 * threadIdx.x};
+    const SMat Lf{sh + 38 * kBranchBlock + 2 * threadIdx.x};
+    const SMat Sc{sh + 60 * kBranchBlock + 2 * threadIdx.x};
     Ctrl *ctrl = G.ctrl;
     if (ctrl->done) return;                    // uniform across the grid
     const int nl = G.nl;
