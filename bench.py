@@ -620,31 +620,40 @@ def run_ours(args):
         for nb in args.sizes:
             g2 = synth.sized_grid(nb, seed=args.seed + rank)
             o2 = dict(rho_pq=args.size_rho[0], rho_va=args.size_rho[1], obj_scale=1.0)
-            s2 = admm.Solver(g2, stream=stream, **o2)
+            # launch shape from the library's tuner (on a separate handle, a few
+            # iterations into a cold solve); every leg of this grid uses it
+            tp = admm.Solver(g2, stream=stream, **o2)
+            tp.solve(tol=0.0, max_iter=5)
+            tb, tbody, _, tl = tp.autotune(2)
+            tp.close()
+            shape = dict(branch_blocks=tb, graph_body_iters=tbody, lanes_per_branch=tl)
+            s2 = admm.Solver(g2, stream=stream, **o2, **shape)
             rec = {"nbus": nb, "nbranch": g2.nbranch, "ngen": g2.ngen,
                    "rho_pq": o2["rho_pq"], "rho_va": o2["rho_va"],
+                   "launch_shape": {"branch_blocks": tb, "graph_body_iters": tbody,
+                                    "lanes_per_branch": tl},
                    "time_to_tol": solve_timed(s2, stream, 1e-3, args.tol_max_iter, False)}
             s2.close()
             # the adaptive outer penalty (beta_rule 1), same grid and penalties
-            s5 = admm.Solver(g2, stream=stream, beta_rule=1, **o2)
+            s5 = admm.Solver(g2, stream=stream, beta_rule=1, **o2, **shape)
             rec["time_to_tol_adaptive_beta"] = solve_timed(s5, stream, 1e-3, args.tol_max_iter,
                                                            False)
             s5.close()
             if args.feasible:
-                s3 = admm.Solver(g2, stream=stream, **dict(o2, rho_pq=args.feas_rho[0],
-                                                          rho_va=args.feas_rho[1]))
+                s3 = admm.Solver(g2, stream=stream, **shape, **dict(o2, rho_pq=args.feas_rho[0],
+                                                                   rho_va=args.feas_rho[1]))
                 rec["time_to_max_viol"] = time_to_violation(s3, stream, args.feas_target,
                                                             args.feas_max_iter, 100)
                 rec["time_to_max_viol"].update({"rho_pq": args.feas_rho[0],
                                                 "rho_va": args.feas_rho[1]})
                 s3.close()
-                s6 = admm.Solver(g2, stream=stream, beta_rule=1,
+                s6 = admm.Solver(g2, stream=stream, beta_rule=1, **shape,
                                  **dict(o2, rho_pq=args.feas_rho[0], rho_va=args.feas_rho[1]))
                 rec["time_to_max_viol_adaptive_beta"] = time_to_violation(
                     s6, stream, args.feas_target, args.feas_max_iter, 100)
                 s6.close()
                 # the one-level variant (z = 0) at its own penalties
-                s4 = admm.Solver(g2, stream=stream, two_level=0,
+                s4 = admm.Solver(g2, stream=stream, two_level=0, **shape,
                                  **dict(o2, rho_pq=args.feas_rho1[0], rho_va=args.feas_rho1[1]))
                 rec["time_to_max_viol_one_level"] = time_to_violation(
                     s4, stream, args.feas_target, args.feas_max_iter, 100)
