@@ -8,22 +8,23 @@
 // handled by an augmented Lagrangian loop around a trust-region Newton method
 // for bound constraints (Lin-More TRON with Steihaug CG, Section III-B).
 //
-// GB300 design.  FP64 runs at 2 FMA/clk/SM (about 1/58 of FP32), so the
-// kernel is bound by FP64 warp instructions, and a warp instruction costs the
-// same whether 32 lanes or 1 lane are active.  Branch problems need very
-// different amounts of work (1 to 20 AL passes, 1 to dozens of TRON
-// iterations), so one-branch-per-thread with a fixed assignment leaves most
-// lanes idle.  Instead the grid is persistent and every lane pulls a new branch
-// from a queue as soon as its branch is finished; each trip of the main loop
-// performs exactly one TRON iteration in every lane that has one to do, so the
-// expensive code runs with nearly full warps.  One lane solves one branch
-// (its Hessian and preconditioner factor packed, 21 entries each, in shared
-// memory, everything else in registers; the TRON free set handled with masks
-// so all loops have fixed trip counts); the branch data the evaluations read
-// (admittances and targets) sit in shared memory too.  The function, gradient and Hessian are evaluated
-// together at every trial point (one sincos), since nearly every trial step is
-// accepted; after a rejected step the gradient and Hessian are re-evaluated at
-// the kept point.
+// GB300 design.  FP64 runs at about 1.7 FMA per clock per SM (0.42 per
+// sub-partition, measured: one warp instruction per ~76 cycles; FP32 is ~76
+// times faster), so the kernel is bound by FP64 warp instructions, and a warp
+// instruction costs the same whether 32 lanes or 1 lane are active.  Branch
+// problems need very different amounts of work (1 to several AL passes, 1 to
+// dozens of TRON iterations), so one-branch-per-thread with a fixed assignment
+// leaves most lanes idle.  Instead the grid is persistent and every lane pulls
+// a new branch from a queue as soon as its branch is finished; each trip of
+// the main loop performs exactly one TRON iteration in every lane that has one
+// to do, so the expensive code runs with nearly full warps.  One lane solves
+// one branch (its Hessian and preconditioner factor packed, 21 entries each,
+// in shared memory, everything else in registers; the TRON free set handled
+// with masks so all loops have fixed trip counts); the branch data the
+// evaluations read (admittances and targets) sit in shared memory too.  The
+// function, gradient and Hessian are evaluated together at every trial point
+// (one sincos), since nearly every trial step is accepted; after a rejected
+// step the gradient and Hessian are re-evaluated at the kept point.
 #include "admm_internal.cuh"
 
 namespace admm {

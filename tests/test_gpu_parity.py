@@ -265,17 +265,20 @@ def test_medium_grid_full_parity(nbus, iters, rho, devices, lanes):
     compare_state(s, o, 1e-9, f"{nbus} lanes {lanes}")
 
 
-def test_full_size_70k_sampled():
-    """The 70k-bus workload in the launch configuration the bench times: three
-    iterations from cold start against the oracle on every coupling (the
-    later ones run on the longest-first queue the earlier ones filed)."""
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_full_size_70k_sampled(lanes):
+    """The 70k-bus workload in the launch configuration the bench times (two
+    blocks per SM, the warps of a block meeting every loop trip; once more
+    with two lanes per branch): three iterations from cold start against the
+    oracle on every coupling (the later ones run on the longest-first queue
+    the earlier ones filed)."""
     grid = synth.sized_grid(70000, seed=1)
     rp, rv, so = synth.penalties_for(70000)
     kw = dict(rho_pq=rp, rho_va=rv, obj_scale=so)
-    s = admm.Solver(grid, **kw)
+    s = admm.Solver(grid, lanes_per_branch=lanes, **kw)
     o = oracle.Oracle(grid, **kw)
     s.solve(tol=0.0, max_iter=3)
     o.solve(tol=0.0, max_iter=3)
-    compare_state(s, o, 1e-9, "70k")
+    compare_state(s, o, 1e-9, f"70k lanes {lanes}")
     st = s.stats()
     assert st["tron_maxiter_hits"] == 0
