@@ -96,6 +96,15 @@ __device__ __forceinline__ double pow2_scale(double v, int k)
     return e > k ? __longlong_as_double(b - ((long long)k << 52)) : 0.0;
 }
 
+// v * 2 by an exponent step on the integer pipe: exact for a normal v below
+// the overflow range; v itself for 0, subnormals, infinities and NaN
+__device__ __forceinline__ double twice(double v)
+{
+    const long long b = __double_as_longlong(v);
+    const unsigned e = (unsigned)((b >> 52) & 0x7ff);
+    return e - 1u < 0x7fdu ? __longlong_as_double(b + (1LL << 52)) : v;
+}
+
 // Two lanes per branch (kL = 2): lanes 2k and 2k+1 hold the same branch and
 // the same state, bit for bit; the parts of a trip that split cleanly (the two
 // line ends' flows, rows of 6x6 products, halves of 6-vector dot products)
@@ -170,13 +179,15 @@ __device__ __forceinline__ void end_terms(bool from, double ap, double aq, doubl
     const double jTq = from ? -jP : jP, iTq = from ? -iP : iP, vTq = from ? -vP : vP;
     const double jPq = from ? jT : -jT, iPq = from ? iT : -iT, vPq = from ? vT : -vT;
     const double vk = from ? vi : vj;
-    const double m2 = 2.0 * mu, wk = rpq + m2;
+    // doublings (2 mu, 2 a, 2 (...)) are exponent steps on the integer pipe
+    const double m2 = twice(mu), wk = rpq + m2;
+    const double ap2 = twice(ap), aq2 = twice(aq);
     // dF = (2a v_i + v_j T, v_i T, vv T') (from end) or (v_j T, 2a v_j + v_i T, vv T');
     // d2F: self term 2a, (0,1) T, (0,2) v_j T', (1,2) v_i T', (2,2) -vv T
-    const double dp0 = from ? 2.0 * ap * vk + jT : jT;
-    const double dp1 = from ? iT : 2.0 * ap * vk + iT;
-    const double dq0 = from ? 2.0 * aq * vk + jTq : jTq;
-    const double dq1 = from ? iTq : 2.0 * aq * vk + iTq;
+    const double dp0 = from ? ap2 * vk + jT : jT;
+    const double dp1 = from ? iT : ap2 * vk + iT;
+    const double dq0 = from ? aq2 * vk + jTq : jTq;
+    const double dq1 = from ? iTq : aq2 * vk + iTq;
     const double dp2 = vP, dq2 = vPq;
     const double rp = Fp - tp, rq = Fq - tq;
     E.fq += rp * rp + rq * rq;
@@ -184,7 +195,7 @@ __device__ __forceinline__ void end_terms(bool from, double ap, double aq, doubl
     E.G0 += cp * dp0 + cq * dq0;
     E.G1 += cp * dp1 + cq * dq1;
     E.G2 += cp * dp2 + cq * dq2;
-    const double sd = 2.0 * (cp * ap + cq * aq);         // c times the self second derivative
+    const double sd = twice(cp * ap + cq * aq);          // c times the self second derivative
     if (from) E.A00 += sd; else E.A11 += sd;
     E.A00 += wk * (dp0 * dp0 + dq0 * dq0);
     E.A11 += wk * (dp1 * dp1 + dq1 * dq1);
@@ -192,9 +203,9 @@ __device__ __forceinline__ void end_terms(bool from, double ap, double aq, doubl
     E.A02 += (cp * jP + cq * jPq) + wk * (dp0 * dp2 + dq0 * dq2);
     E.A12 += (cp * iP + cq * iPq) + wk * (dp1 * dp2 + dq1 * dq2);
     E.A22 += -(cp * vT + cq * vTq) + wk * (dp2 * dp2 + dq2 * dq2);
-    e0 = 2.0 * (Fp * dp0 + Fq * dq0);
-    e1 = 2.0 * (Fp * dp1 + Fq * dq1);
-    e2 = 2.0 * (Fp * dp2 + Fq * dq2);
+    e0 = twice(Fp * dp0 + Fq * dq0);
+    e1 = twice(Fp * dp1 + Fq * dq1);
+    e2 = twice(Fp * dp2 + Fq * dq2);
 }
 
 // f, gradient, packed Hessian and the four flows of eq. branch at x.
@@ -241,21 +252,22 @@ __device__ __forceinline__ void evaluate1(const double *sY, const double *sT, do
     const double A22 = E.A22 + (r02 * e02 + r12 * e12);
     const double rwi = wi - sT[4 * S], rti = x[2] - sT[5 * S];
     const double rwj = wj - sT[6 * S], rtj = x[3] - sT[7 * S];
-    f = 0.5 * rpq * E.fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
-      + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
-    g[0] = E.G0 + 2.0 * rva * rwi * vi;
-    g[1] = E.G1 + 2.0 * rva * rwj * vj;
+    const double hrt = pow2_scale(rt, 1), trva = twice(rva);
+    f = pow2_scale(rpq, 1) * E.fq + pow2_scale(rva, 1) * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
+      + lt0 * h0 + hrt * h0 * h0 + lt1 * h1 + hrt * h1 * h1;
+    g[0] = E.G0 + trva * rwi * vi;
+    g[1] = E.G1 + trva * rwj * vj;
     g[2] = E.G2 + rva * rti;
     g[3] = -E.G2 + rva * rtj;
     g[4] = mu0;
     g[5] = mu1;
-    H[P(0, 0)] = A00 + rva * (4.0 * wi + 2.0 * rwi);
+    H[P(0, 0)] = A00 + rva * (4.0 * wi + twice(rwi));
     H[P(0, 1)] = A01;
     H[P(0, 2)] = A02;
     H[P(0, 3)] = -A02;
     H[P(0, 4)] = r00;
     H[P(0, 5)] = r10;
-    H[P(1, 1)] = A11 + rva * (4.0 * wj + 2.0 * rwj);
+    H[P(1, 1)] = A11 + rva * (4.0 * wj + twice(rwj));
     H[P(1, 2)] = A12;
     H[P(1, 3)] = -A12;
     H[P(1, 4)] = r01;
@@ -331,21 +343,22 @@ __device__ __forceinline__ void evaluate2(unsigned m, const double *sY, const do
     const double wi = vi * vi, wj = vj * vj;
     const double rwi = wi - sT[4 * S], rti = x[2] - sT[5 * S];
     const double rwj = wj - sT[6 * S], rtj = x[3] - sT[7 * S];
-    f = 0.5 * rpq * fq + 0.5 * rva * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
-      + lt0 * h0 + 0.5 * rt * h0 * h0 + lt1 * h1 + 0.5 * rt * h1 * h1;
-    g[0] = G0 + 2.0 * rva * rwi * vi;
-    g[1] = G1 + 2.0 * rva * rwj * vj;
+    const double hrt = pow2_scale(rt, 1), trva = twice(rva);
+    f = pow2_scale(rpq, 1) * fq + pow2_scale(rva, 1) * (rwi * rwi + rti * rti + rwj * rwj + rtj * rtj)
+      + lt0 * h0 + hrt * h0 * h0 + lt1 * h1 + hrt * h1 * h1;
+    g[0] = G0 + trva * rwi * vi;
+    g[1] = G1 + trva * rwj * vj;
     g[2] = G2 + rva * rti;
     g[3] = -G2 + rva * rtj;
     g[4] = mu0;
     g[5] = mu1;
-    H[P(0, 0)] = A00 + rva * (4.0 * wi + 2.0 * rwi);
+    H[P(0, 0)] = A00 + rva * (4.0 * wi + twice(rwi));
     H[P(0, 1)] = A01;
     H[P(0, 2)] = A02;
     H[P(0, 3)] = -A02;
     H[P(0, 4)] = r00;
     H[P(0, 5)] = r10;
-    H[P(1, 1)] = A11 + rva * (4.0 * wj + 2.0 * rwj);
+    H[P(1, 1)] = A11 + rva * (4.0 * wj + twice(rwj));
     H[P(1, 2)] = A12;
     H[P(1, 3)] = -A12;
     H[P(1, 4)] = r01;
@@ -447,7 +460,7 @@ __device__ __forceinline__ double half_quad(SMat H, const double *v, unsigned m 
         double q = 0.0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            double t = 0.5 * H[P(i, i)] * v[i];
+            double t = pow2_scale(H[P(i, i)], 1) * v[i];
 #pragma unroll
             for (int j = i + 1; j < 6; ++j) t += H[P(i, j)] * v[j];
             q += v[i] * t;
