@@ -96,14 +96,16 @@ __device__ __forceinline__ double pow2_scale(double v, int k)
     return e > k ? __longlong_as_double(b - ((long long)k << 52)) : 0.0;
 }
 
-// v * 2 by an exponent step on the integer pipe: exact for a normal v below
-// the overflow range; v itself for 0, subnormals, infinities and NaN
-__device__ __forceinline__ double twice(double v)
+// v * 2^k for k >= 0 by an exponent step on the integer pipe: exact for a
+// normal v whose result stays finite; v itself for 0, subnormals, infinities,
+// NaN and results that would overflow
+__device__ __forceinline__ double pow2_up(double v, int k)
 {
     const long long b = __double_as_longlong(v);
-    const unsigned e = (unsigned)((b >> 52) & 0x7ff);
-    return e - 1u < 0x7fdu ? __longlong_as_double(b + (1LL << 52)) : v;
+    const long long e = (b >> 52) & 0x7ff;
+    return (e != 0 && e + k < 0x7ff) ? __longlong_as_double(b + ((long long)k << 52)) : v;
 }
+__device__ __forceinline__ double twice(double v) { return pow2_up(v, 1); }
 
 // Two lanes per branch (kL = 2): lanes 2k and 2k+1 hold the same branch and
 // the same state, bit for bit; the parts of a trip that split cleanly (the two
@@ -578,7 +580,7 @@ __device__ __forceinline__ void cauchy(bool on, const Bounds &B, const double *x
         // the path stops moving once a is past every breakpoint
         if (go && !back) go = !pa;
         if (!__any_sync(kFull, go)) break;
-        const double an = back ? a * 0.1 : a * 10.0;
+        const double an = a * (back ? 0.1 : 10.0);
         if (go) c.cauchy++;
         double qn;
         bool pn;
@@ -908,7 +910,7 @@ __device__ __forceinline__ void subspace(bool on, const Bounds &B, const double 
         }
         qs = okp ? qb : qs;
         ps = ps && !okp;
-        beta *= 0.5;
+        beta = pow2_scale(beta, 1);                 // 2^-(t+1), exact
     }
 }
 
@@ -1222,8 +1224,10 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
             const bool below1 = !trusted && dlt(actred, kEta1 * prered);
             const bool above2 = trusted || dlt(kEta2 * prered, actred);
             const bool above0 = trusted || dlt(kEta0 * prered, actred);
-            if (below1) dsq = (kSigma1 * kSigma1) * dmini(snorm2, dsq);
-            else if (above2) dsq = dmaxi(dsq, (kSigma3 * kSigma3) * snorm2);
+            // sigma1^2 = 2^-4 and sigma3^2 = 2^4: exponent steps
+            static_assert(kSigma1 * kSigma1 == 0.0625 && kSigma3 * kSigma3 == 16.0, "radius factors");
+            if (below1) dsq = pow2_scale(dmini(snorm2, dsq), 4);
+            else if (above2) dsq = dmaxi(dsq, pow2_up(snorm2, 4));
             if (above0) {
 #pragma unroll
                 for (int i = 0; i < 6; ++i) x[i] = xt[i];
