@@ -1199,9 +1199,13 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
             f = fe;
             c.tron_calls++;
             c.fgh++;
-            gtol = O.tron_gtol * dmaxi(pgnorm(B, x, g), 1.0);
-            double sp[6];
+            // the projected-gradient step P(x - g) - x gives both the stopping
+            // threshold (its max norm) and the first trust radius (its 2-norm)
+            double sp[6], pg0 = 0.0;
             pstep(B, x, g, 1.0, sp);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) pg0 = amax(pg0, sp[i]);
+            gtol = O.tron_gtol * dmaxi(pg0, 1.0);
             dsq = dot6<kL>(sp, sp, im);
             alpha = dpos(alpha) ? alpha : 1.0;   // carried from the previous call
             k = 0;
@@ -1221,7 +1225,8 @@ __device__ __forceinline__ void branch_tron_body(DevGrid G, DevOpts O)
             // the rounding level of f - ft, whichever way the constant of
             // eq. branch is written
             const bool trusted = dle(prered, O.tron_ftol * fa);
-            const bool below1 = !trusted && dlt(actred, kEta1 * prered);
+            static_assert(kEta1 == 0.25, "eta1 scaling is an exponent step");
+            const bool below1 = !trusted && dlt(actred, pow2_scale(prered, 2));
             const bool above2 = trusted || dlt(kEta2 * prered, actred);
             const bool above0 = trusted || dlt(kEta0 * prered, actred);
             // sigma1^2 = 2^-4 and sigma3^2 = 2^4: exponent steps
