@@ -624,7 +624,7 @@ def run_ours(args):
             # iterations into a cold solve); every leg of this grid uses it
             tp = admm.Solver(g2, stream=stream, **o2)
             tp.solve(tol=0.0, max_iter=5)
-            tb, tbody, _, tl = tp.autotune(2)
+            tb, tbody, _, tl = tp.autotune(4)
             tp.close()
             shape = dict(branch_blocks=tb, graph_body_iters=tbody, lanes_per_branch=tl)
             s2 = admm.Solver(g2, stream=stream, **o2, **shape)
@@ -672,7 +672,7 @@ def run_ours(args):
                     sl.close()
                 st_ = admm.Solver(g2, stream=stream, **o2)
                 st_.solve(tol=0.0, max_iter=5)
-                tb, tbody, tms, tl = st_.autotune(2)
+                tb, tbody, tms, tl = st_.autotune(4)
                 st_.close()
                 lc.update({"autotuned_lanes_per_branch": tl, "autotuned_branch_blocks": tb,
                            "autotuned_branch_ms": tms})
@@ -706,7 +706,7 @@ def run_ours(args):
         tgrid = synth.sized_grid(10000, seed=args.seed + 100 + rank)
         topts = dict(rho_pq=3e3, rho_va=3e4, obj_scale=1.0)
         ts = admm.Solver(tgrid, stream=stream, **topts)
-        tuned_t = ts.autotune(2)        # launch shape for this grid (state put back)
+        tuned_t = ts.autotune(4)        # launch shape for this grid (state put back)
         pds, qds = synth.ar1_loads(tgrid, args.track_steps, seed=args.seed + 200 + rank)
         pmaxs = tracking.renewable_pmax(tgrid, args.track_steps, seed=args.seed + 300 + rank)
         cold, recs = tracking.run_tracking(ts, tgrid, pds, qds, pmaxs, tol=1e-3, max_iter=5000,
