@@ -1335,6 +1335,15 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
         const int need = branch_blocks_needed(h->nl, clan[c]);
         return cand[c] < need ? (cand[c] > 0 ? cand[c] : 1) : need;
     };
+    // candidates that come out as the same launch (blocks capped at the
+    // branches' need) are timed once: timing one shape several times and
+    // keeping its best would favour it over shapes timed once
+    bool dup[kCand];
+    for (int c = 0; c < kCand; ++c) {
+        dup[c] = false;
+        for (int e = 0; e < c; ++e)
+            dup[c] = dup[c] || (clan[e] == clan[c] && blocks_of(e) == blocks_of(c));
+    }
     size_t bytes = 0;
     for (auto &p : replay_parts(h)) bytes += (p.second + 255) & ~(size_t)255;
     char *snap = nullptr;
@@ -1351,6 +1360,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
     for (int pass = 0; pass < 2 && rc == ADMM_OK; ++pass) {
         for (int k = 0; k < kCand && rc == ADMM_OK; ++k) {
             const int c = pass == 0 ? k : kCand - 1 - k;
+            if (dup[c]) continue;
             const int nbk = blocks_of(c);
             DevGrid G = h->G;
             G.nblk_branch = nbk;
@@ -1376,7 +1386,7 @@ extern "C" int admm_autotune(admm_handle *h, int32_t iters, int32_t *blocks_out,
     }
     int best = 0;
     for (int c = 1; c < kCand; ++c)
-        if (tot[c] < tot[best]) best = c;
+        if (!dup[c] && tot[c] < tot[best]) best = c;
     const int nbk = blocks_of(best);
     if (rc == ADMM_OK) {
         h->nblk_branch = nbk;
