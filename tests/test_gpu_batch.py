@@ -89,6 +89,32 @@ def test_batched_scenarios_match_oracle():
     b.close()
 
 
+def test_large_batch_with_trip_barrier_matches_oracle():
+    """A batch with more branches than one block per SM holds (four 10k-bus
+    grids, ~50,000 branches): the default launch then runs two blocks per SM
+    whose warps meet every loop trip.  Every scenario against the oracle at
+    1e-9 after four iterations, one of them begun two iterations late."""
+    grids = [synth.sized_grid(10000, seed=21 + k, devices=(k == 1)) for k in range(4)]
+    kw = dict(rho_pq=3e3, rho_va=3e4)
+    b = admm.Solver(grids, **kw)
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert sum(g.nbranch for g in grids) >= 2 * sms * 128   # two blocks per SM by default
+    for k in (0, 1, 2):
+        b.slot_begin(k, tol=0.0, max_iter=4)
+    b.run(2)
+    b.slot_begin(3, tol=0.0, max_iter=4)               # joins two iterations late
+    b.run(100)
+    st, it = b.slot_status()
+    assert list(it) == [4, 4, 4, 4]
+    for k, g in enumerate(grids):
+        o = oracle.Oracle(g, **kw)
+        o.solve(tol=0.0, max_iter=4)
+        b.select(k)
+        compare_state(b, o, 1e-9, f"scenario {k}")
+    b.close()
+
+
 def test_continuous_batching_slots_follow_solo_trajectories():
     grids = [synth.tiny_grid(12), synth.tiny_grid(13), synth.sized_grid(400, seed=5)]
     b = admm.Solver(grids, **TINY)
